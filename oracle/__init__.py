@@ -1,0 +1,28 @@
+"""Plain, slow, obviously-correct CPU oracle for the state-vector simulator of
+arXiv:1805.04708 (JUQCS).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product package may import this
+package; only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline``
+leg / ``--impl reference`` arm of ``bench.py`` use it.  It shares no code with
+the CUDA path: its gate table is retyped from the paper's instruction set
+(Appendix A), its arithmetic is numpy complex128 (FP64), and its reductions are
+compensated FP64 sums.
+
+Modules
+-------
+gates     : the 2x2 / 4x4 / 8x8 matrices of Appendix A.
+statevec  : |0..0>, the pair update of Eq. (NUM2) for any U(2) with 0..2
+            controls, dense k-qubit gates, index permutations, SHORBOX, the
+            projections CLEAR/SET, and the reductions (norm Eq. (STAT1),
+            single-qubit probabilities of Sec. 2, BEGIN MEASUREMENT, register
+            marginals).
+adapt2    : the 2-byte adaptive polar encoding of Sec. 4.1, step by step.
+shor      : the classical side of Shor's algorithm (Sec. 5.4) and the
+            closed-form x-register distribution after SHORBOX + QFT.
+circuit   : runs a gate list (mnemonic records) through statevec / adapt2.
+
+Parity pins: every function here is pinned in ``tests/test_oracle_*.py``
+against brute force, closed forms or the paper's printed tables.  Functions
+without such a pin are listed as "parity unpinned" in their docstring (none at
+present).
+"""
