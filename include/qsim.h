@@ -1,0 +1,216 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector engine (libqsim.so).
+ *
+ * The engine holds the 2^N complex amplitudes of an N-qubit quantum computer
+ * (Sec. 2, Eq. (STAT2) of arXiv:1805.04708) in device memory and updates them
+ * in place with hand-written sm_103a CUDA kernels.  Qubit q is bit q of the
+ * basis index, qubit 0 the least significant ("rightmost") bit (Sec. 2, the
+ * paragraph after Eq. (STAT1)).
+ *
+ * Conventions for every entry point
+ *  - Plain C types only; device pointers are marked "device", host pointers
+ *    "host".  The caller owns every host array it passes, and allocates every
+ *    output array.
+ *  - Calls are ordered on the stream given at creation (NULL = the legacy
+ *    default stream).  Gate calls return once the work is enqueued; calls that
+ *    return numbers to the host (norm, expect_xyz, measure_probs, copy_out)
+ *    synchronise that stream before returning.
+ *  - Invalid arguments are rejected before anything is launched, with
+ *    QS_EINVAL (qubit out of range, repeated qubit, N out of range, bad
+ *    sizes), QS_ENOTUNITARY (a matrix further than the stated tolerance from
+ *    unitary) or QS_ENOTBIJECTIVE (a permutation table that is not a
+ *    bijection).  CUDA failures return QS_ECUDA; qs_last_error_string() then
+ *    describes the error.  Nothing aborts the process.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+/* Storage encodings of one amplitude.
+ *  QS_C128  : complex128, interleaved (re, im) FP64, 16 B per amplitude (the
+ *             double-precision form of JUQCS-E, Sec. 4.1).
+ *  QS_C64   : complex64, interleaved (re, im) FP32, 8 B per amplitude.
+ *  QS_ADAPT2: the 2-byte adaptive polar code of JUQCS-A (Sec. 4.1): one
+ *             little-endian 16-bit word per amplitude, low byte b0 (magnitude
+ *             code), high byte b1 (angle code), both two's-complement int8,
+ *             plus the state-wide pair (r0, r1) kept by the handle. */
+typedef enum { QS_C128 = 0, QS_C64 = 1, QS_ADAPT2 = 2 } qs_encoding;
+
+typedef enum {
+  QS_OK = 0,
+  QS_EINVAL = 1,
+  QS_ENOMEM = 2,
+  QS_ENOTBIJECTIVE = 3,
+  QS_ECUDA = 4,
+  QS_ETIMEOUT = 5,
+  QS_EZEROPROJ = 6,
+  QS_ENOTUNITARY = 7,
+  QS_EUNSUPPORTED = 8
+} qs_status;
+
+typedef struct qs_sim qs_sim; /* opaque; owns or borrows its device state */
+
+/* A gate record: a 2x2 complex matrix u applied to qubit `target` on the
+ * subspace where the nc qubits controls[0..nc-1] are all 1 (nc = 0, 1, 2).
+ * This covers every gate of the instruction set (Appendix A): single-qubit
+ * gates (nc = 0), CNOT and U(k) (nc = 1), TOFFOLI (nc = 2); the update is the
+ * pair rule of Eq. (NUM2) with H replaced by u (Eq. (AQS0)).
+ * u is row-major with interleaved (re, im): u00, u01, u10, u11. */
+typedef struct {
+  int32_t nc;
+  int32_t controls[2];
+  int32_t target;
+  double u[8];
+} qs_gate;
+
+/* ---- errors ------------------------------------------------------------- */
+/* Text of the last error on this thread (static storage, never NULL). */
+const char* qs_last_error_string(void);
+/* Library version string, e.g. "qsim 0.1 sm_103a". */
+const char* qs_version(void);
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t qs_kernel_launches(void);
+
+/* ---- lifetime (QUBITS N, Appendix A; |0..0> of Eq. (appa0)) -------------- */
+/* Create an N-qubit state |0...0> (a_0 = 1, every other amplitude 0) in
+ * encoding `enc`, in device memory the handle allocates and owns.
+ * 1 < N < 64 (Appendix A, QUBITS); N must also fit the device memory
+ * (2^N * 16, 8 or 2 bytes), else QS_ENOMEM.  cuda_stream is a cudaStream_t
+ * (NULL = default stream) used by every later call on the handle. */
+qs_status sim_create(int N, qs_encoding enc, void* cuda_stream, qs_sim** out);
+
+/* As sim_create, but the state lives in a caller-owned device buffer
+ * (dev_ptr, `bytes` >= 2^N * bytes-per-amplitude, 256-byte aligned), e.g. a
+ * torch tensor's storage.  The caller keeps ownership and must keep the
+ * buffer alive until sim_destroy.  The buffer is overwritten with |0..0>. */
+qs_status sim_create_in(int N, qs_encoding enc, void* dev_ptr, size_t bytes,
+                        void* cuda_stream, qs_sim** out);
+
+/* Release the handle and the device memory it owns (never a borrowed
+ * buffer).  Synchronises the handle's stream first. */
+qs_status sim_destroy(qs_sim* sim);
+
+/* Number of qubits, encoding, device pointer of the amplitudes and their size
+ * in bytes. */
+qs_status sim_info(const qs_sim* sim, int* N, int* enc, void** dev_ptr, size_t* bytes);
+
+/* Reset to |0..0> (a_0 = 1). */
+qs_status sim_reset(qs_sim* sim);
+
+/* ---- gates (Sec. 2, Eq. (NUM2); Appendix A) ------------------------------ */
+/* Single-qubit gate: for every basis index i with bit `target` = 0,
+ * (a_i, a_{i+2^target}) <- U (a_i, a_{i+2^target}) (Eq. (NUM2), Eq. (AQS0)).
+ * U: host, 8 doubles, row-major (re, im) of u00, u01, u10, u11; it must be
+ * unitary to 1e-10 (max-abs of U U^dagger - 1), else QS_ENOTUNITARY.
+ * Diagonal, anti-diagonal and Hadamard-shaped matrices run specialised
+ * kernels that give the same result. */
+qs_status apply_gate(qs_sim* sim, int target, const double U[8]);
+
+/* Controlled gate: the same update restricted to the indices whose nc
+ * control bits are all 1 (nc in {0,1,2}; CNOT, U(k), TOFFOLI of Appendix A;
+ * the groups of four and eight amplitudes described after Eq. (NUM2)).
+ * controls: host, nc distinct qubits, none equal to target. */
+qs_status apply_controlled(qs_sim* sim, const int* controls, int nc, int target,
+                           const double U[8]);
+
+/* Dense k-qubit gate (1 <= k <= 5): a 2^k x 2^k complex matrix applied to the
+ * amplitudes of each group of 2^k basis states that differ only in the
+ * qubits `qubits` (Eq. (AQS0) for n-qubit gates; the fused multi-qubit gates
+ * proposed at the end of Sec. 5.2).  Bit m of the local row/column index is
+ * the value of qubits[m].  U: host, 2*4^k doubles, row-major (re, im).
+ * The matrix must be unitary to 1e-10. */
+qs_status apply_fused(qs_sim* sim, const int* qubits, int k, const double* U);
+
+/* Controlled register permutation (SHORBOX's f(x) = y^x mod G built from
+ * controlled modular multiplications, Sec. 5.4): on every basis index whose
+ * nc control bits are all 1, the value f of the register bits
+ * reg_lo .. reg_lo+reg_w-1 is replaced by table[f].  table: host, 2^reg_w
+ * uint32 entries forming a bijection of [0, 2^reg_w), else QS_ENOTBIJECTIVE.
+ * Amplitudes (or ADAPT2 codes) move bit-exactly.  1 <= reg_w <= 12; controls
+ * must lie outside the register. */
+qs_status apply_permutation(qs_sim* sim, const int* controls, int nc, int reg_lo,
+                            int reg_w, const uint32_t* table);
+
+/* Fill `table` (host, 2^width uint32) with f -> a*f mod G for f < G and the
+ * identity for G <= f < 2^width (the controlled multiplication of Sec. 5.4).
+ * Requires gcd(a, G) = 1 and G <= 2^width. */
+qs_status modmul_table(uint64_t a, uint64_t G, int width, uint32_t* table);
+
+/* SHORBOX nx G y (Appendix A): overwrite the state with
+ * 2^{-nx/2} sum_{x=0}^{2^nx - 1} |x>|y^x mod G>: x-register on qubits
+ * 0..nx-1, f-register on qubits nx..N-1 (G <= 2^{N-nx}, 1 <= y < G).
+ * One write sweep, no gate is applied. */
+qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
+
+/* ---- circuits ----------------------------------------------------------- */
+/* Run a gate list in order.  mode 0: one kernel per gate (the per-gate sweep
+ * of Sec. 3).  mode 1: the native planner groups consecutive gates into
+ * shared-memory tile passes (several gates per read and write of the state;
+ * the fusion strategy suggested at the end of Sec. 5.2) and runs each pass as
+ * one kernel.  Results equal mode 0 up to floating-point rounding order.
+ * gates: host array of n records.  n_passes (may be NULL) receives the
+ * number of state sweeps launched. */
+qs_status circuit_run(qs_sim* sim, const qs_gate* gates, int n, int mode, int* n_passes);
+
+/* As circuit_run, and records a CUDA event pair around every sweep on the
+ * handle's stream: pass_ms (host, room for max_passes floats, may be NULL)
+ * receives the device time of each sweep in order.  Synchronises the stream
+ * before returning. */
+qs_status circuit_run_timed(qs_sim* sim, const qs_gate* gates, int n, int mode, int* n_passes,
+                            float* pass_ms, int max_passes);
+
+/* Build a gate record from an instruction-set mnemonic (Appendix A):
+ * "I","H","X","Y","Z","S","S+","T","T+","U1","U2","U3","+X","-X","+Y","-Y",
+ * "R" (params[0] = k, negative for R^dagger), "CNOT", "U" (params[0] = k),
+ * "TOFFOLI", plus "RZ" (params[0] = theta: diag(e^{-i theta/2}, e^{i theta/2}))
+ * and "MAT"/"CMAT" (params = 8 doubles of an explicit U).  qubits: host, the
+ * mnemonic's qubit operands in the paper's order (controls first). */
+qs_status gate_std(const char* mnemonic, const int* qubits, int nqubits,
+                   const double* params, int nparams, qs_gate* out);
+
+/* ---- reductions (Sec. 2 probabilities; BEGIN MEASUREMENT, Appendix A) ----- */
+/* The "norm" call: <Phi|Phi> = sum_i |a_i|^2 (Eq. (STAT1)), accumulated in
+ * FP64 with compensation, in a fixed order (bit-stable run to run).  Named
+ * sim_norm because the CUDA math library already exports a C function norm. */
+qs_status sim_norm(qs_sim* sim, double* out);
+
+/* BEGIN MEASUREMENT (Appendix A): for every qubit n = 0..N-1,
+ * qx[n] = <(1 - sigma^x_n)>/2, qy[n] = <(1 - sigma^y_n)>/2,
+ * qz[n] = <(1 - sigma^z_n)>/2, i.e. with w_n = sum_{bit n = 0} conj(a_i) a_{i+2^n}:
+ * qx = <Phi|Phi>/2 - Re w_n, qy = <Phi|Phi>/2 - Im w_n, qz = P(qubit n = 1).
+ * qx, qy, qz: host arrays of N doubles.  The state is unchanged. */
+qs_status expect_xyz(qs_sim* sim, double* qx, double* qy, double* qz);
+
+/* Marginal distribution of the nq qubits `qubits` (Sec. 2: the probability
+ * of outcome 0/1 for a single qubit, generalised to a register):
+ * out[k] = sum over basis states whose qubit qubits[m] equals bit m of k of
+ * |a|^2, for k = 0..2^nq - 1 (1 <= nq <= 24).  out: host, 2^nq doubles. */
+qs_status measure_probs(qs_sim* sim, const int* qubits, int nq, double* out);
+
+/* ---- raw state access (parity dumps) ------------------------------------- */
+/* Copy the raw amplitudes (2^N * bytes-per-amplitude bytes, layout as in
+ * qs_encoding) to / from host memory.  For QS_ADAPT2, r0r1 (host, 2 doubles,
+ * may be NULL on copy_out) carries (r0, r1). */
+qs_status sim_copy_out(qs_sim* sim, void* host, size_t bytes, double* r0r1);
+qs_status sim_copy_in(qs_sim* sim, const void* host, size_t bytes, const double* r0r1);
+
+/* Wait for every call enqueued on the handle's stream. */
+qs_status sim_sync(qs_sim* sim);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

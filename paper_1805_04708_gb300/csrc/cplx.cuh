@@ -1,0 +1,81 @@
+// Complex helpers and the 2x2 update functors shared by the dense-encoding
+// kernels (per-gate sweeps and shared-memory tile passes).
+#pragma once
+#include <cuda_runtime.h>
+
+template <typename R> struct Cx { R x, y; };
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cx(R x, R y) { Cx<R> c; c.x = x; c.y = y; return c; }
+
+// a * f, exact for the unit factors (code 0: 1, 1: i, 2: -1, 3: -i).
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul_code(Cx<R> a, Cx<R> f, int code) {
+  switch (code) {
+    case 0: return a;
+    case 1: return cx<R>(-a.y, a.x);
+    case 2: return cx<R>(-a.x, -a.y);
+    case 3: return cx<R>(a.y, -a.x);
+    default: return cx<R>(a.x * f.x - a.y * f.y, a.x * f.y + a.y * f.x);
+  }
+}
+
+// u0 * a0 + u1 * a1
+template <typename R>
+__device__ __forceinline__ Cx<R> cmac2(Cx<R> u0, Cx<R> a0, Cx<R> u1, Cx<R> a1) {
+  R re = u0.x * a0.x;
+  re = fma(-u0.y, a0.y, re);
+  re = fma(u1.x, a1.x, re);
+  re = fma(-u1.y, a1.y, re);
+  R im = u0.x * a0.y;
+  im = fma(u0.y, a0.x, im);
+  im = fma(u1.x, a1.y, im);
+  im = fma(u1.y, a1.x, im);
+  return cx<R>(re, im);
+}
+
+// Storage <-> Cx conversions.
+__device__ __forceinline__ Cx<double> ld(const double2& v) { return cx<double>(v.x, v.y); }
+__device__ __forceinline__ Cx<float> ld(const float2& v) { return cx<float>(v.x, v.y); }
+__device__ __forceinline__ void st(double2& v, Cx<double> a) { v.x = a.x; v.y = a.y; }
+__device__ __forceinline__ void st(float2& v, Cx<float> a) { v.x = a.x; v.y = a.y; }
+
+// ---------------------------------------------------------------------------
+// 2x2 update functors.  pair(a0, a1) updates the two amplitudes of one pair
+// (Eq. (NUM2) with the gate's matrix); one(a) multiplies one amplitude.
+// ---------------------------------------------------------------------------
+template <typename R> struct OpDense {
+  Cx<R> u00, u01, u10, u11;
+  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
+    Cx<R> b0 = cmac2(u00, a0, u01, a1);
+    Cx<R> b1 = cmac2(u10, a0, u11, a1);
+    a0 = b0; a1 = b1;
+  }
+};
+template <typename R> struct OpHad {
+  R s;
+  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
+    Cx<R> b0 = cx<R>((a0.x + a1.x) * s, (a0.y + a1.y) * s);
+    Cx<R> b1 = cx<R>((a0.x - a1.x) * s, (a0.y - a1.y) * s);
+    a0 = b0; a1 = b1;
+  }
+};
+template <typename R> struct OpDiag {
+  Cx<R> d0, d1; int c0, c1;
+  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
+    a0 = cmul_code(a0, d0, c0);
+    a1 = cmul_code(a1, d1, c1);
+  }
+};
+template <typename R> struct OpAnti {
+  Cx<R> f01, f10; int c0, c1;
+  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
+    Cx<R> b0 = cmul_code(a1, f01, c0);
+    Cx<R> b1 = cmul_code(a0, f10, c1);
+    a0 = b0; a1 = b1;
+  }
+};
+template <typename R> struct OpMul {
+  Cx<R> f; int c;
+  __device__ __forceinline__ void one(Cx<R>& a) const { a = cmul_code(a, f, c); }
+};

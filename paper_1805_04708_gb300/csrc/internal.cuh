@@ -1,0 +1,137 @@
+// Internal declarations shared by the translation units of libqsim.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "qsim.h"
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct qs_sim {
+  int N;
+  qs_encoding enc;
+  cudaStream_t stream;
+  void* state;        // device amplitudes
+  size_t bytes;       // 2^N * bytes per amplitude
+  bool owns;          // state allocated by the handle
+  double r0, r1;      // ADAPT2 magnitude range (Sec. 4.1)
+  void* scratch;      // device scratch for reductions and ADAPT2 range passes
+  size_t scratch_bytes;
+  void* hbuf;         // pinned host staging for results
+  size_t hbuf_bytes;
+  int device;
+  int num_sms;
+};
+
+// error reporting ------------------------------------------------------------
+void qs_set_error(const char* fmt, ...);
+#define QS_CUDA(call)                                                         \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      qs_set_error("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                 \
+      return QS_ECUDA;                                                        \
+    }                                                                         \
+  } while (0)
+void qs_count_launch(void);
+#define QS_LAUNCH_CHECK()          \
+  do {                             \
+    qs_count_launch();             \
+    QS_CUDA(cudaGetLastError());   \
+  } while (0)
+#define QS_TRY(x)                      \
+  do {                                 \
+    qs_status s_ = (x);                \
+    if (s_ != QS_OK) return s_;        \
+  } while (0)
+
+static inline size_t qs_amp_bytes(qs_encoding e) {
+  return e == QS_C128 ? 16 : (e == QS_C64 ? 8 : 2);
+}
+
+// ---------------------------------------------------------------------------
+// gate classification (host)
+// ---------------------------------------------------------------------------
+// Kinds of 2x2 update, each giving the same result as the dense product:
+enum GateKind : int {
+  GK_DENSE = 0,   // general u
+  GK_HAD = 1,     // s * [[1, 1], [1, -1]], s real
+  GK_DIAG = 2,    // diag(d0, d1)
+  GK_ANTI = 3,    // [[0, f01], [f10, 0]]
+  GK_IDENT = 4    // identity (no-op)
+};
+// Unit factors multiply exactly: 0 = 1, 1 = i, 2 = -1, 3 = -i, 4 = general.
+struct GateClass {
+  int kind;
+  int c0, c1;        // unit codes of the two factors (diag: d0, d1; anti: f01, f10)
+};
+GateClass classify_u2(const double u[8]);
+int unit_code(double re, double im);
+
+// Unitarity check: max-abs of U U^dagger - 1 over a d x d matrix (row-major
+// interleaved re, im).
+double unitarity_defect(const double* U, int d);
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns QS_OK or QS_ECUDA)
+// ---------------------------------------------------------------------------
+// Controlled 2x2 update on the dense encodings (C128 / C64).
+qs_status launch_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]);
+// Dense k-qubit gate (C128 / C64).
+qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* U);
+// Register permutation (all encodings).
+qs_status launch_permutation(qs_sim* s, const int* controls, int nc, int reg_lo, int reg_w,
+                             const uint32_t* table);
+qs_status launch_shorbox(qs_sim* s, int nx, uint64_t G, uint64_t y);
+qs_status launch_reset(qs_sim* s);
+// Reductions (all encodings); results on the host.
+qs_status launch_norm(qs_sim* s, double* out);
+qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz);
+qs_status launch_marginal(qs_sim* s, const int* qubits, int nq, double* out);
+
+// Tile passes --------------------------------------------------------------------
+// One gate inside a shared-memory tile pass.
+struct TileOp {
+  int kind;            // GateKind; GK_DIAG with target outside the tile = "outer"
+  int c0, c1;          // unit codes
+  int p;               // local bit of the target (-1: target outside the tile)
+  uint32_t lmask;      // local control mask (bits of the tile index)
+  uint64_t gmask;      // outer control mask (global index bits, fixed per tile)
+  uint64_t gtbit;      // outer target bit (global), for outer diagonals
+  double u[8];
+};
+struct TilePass {
+  int b;               // tile bits
+  int bits[16];        // global positions of the tile bits, ascending
+  int nops;
+  int op_begin;        // index into the op array
+};
+// Plan a gate list into tile passes (greedy, gate order preserved).
+int plan_tile_passes(const qs_gate* gates, int n, int N, int b, int low_bits,
+                     TilePass* passes, int max_passes, TileOp* ops, int max_ops);
+qs_status launch_tile_pass(qs_sim* s, const TilePass& pass, const TileOp* ops);
+
+// ADAPT2 --------------------------------------------------------------------------
+qs_status a2_apply_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]);
+qs_status a2_norm(qs_sim* s, double* out);
+qs_status a2_expect(qs_sim* s, double* qx, double* qy, double* qz);
+qs_status a2_marginal(qs_sim* s, const int* qubits, int nq, double* out);
+qs_status a2_shorbox(qs_sim* s, int nx, uint64_t G, uint64_t y);
+qs_status a2_reset(qs_sim* s);
+
+// scratch management
+qs_status ensure_scratch(qs_sim* s, size_t bytes);
+qs_status ensure_hbuf(qs_sim* s, size_t bytes);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+// Insert a zero bit at position b of x.
+__device__ __forceinline__ uint64_t ins0(uint64_t x, int b) {
+  uint64_t lo = x & ((1ull << b) - 1);
+  return ((x >> b) << (b + 1)) | lo;
+}
+#endif

@@ -1,0 +1,321 @@
+"""ctypes binding of libqsim.so (include/qsim.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels.  PyTorch supplies device memory (a state can live in a torch
+tensor's storage) and the CUDA stream.  Importing this module loads the
+compiled library and raises ImportError when it is missing: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsim.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libqsim.so is not built (run paper_1805_04708_gb300.build.build() or "
+        "__graft_entry__.build()); the simulator has no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+C128, C64, ADAPT2 = 0, 1, 2
+ENCODINGS = {"c128": C128, "c64": C64, "adapt2": ADAPT2}
+AMP_BYTES = {C128: 16, C64: 8, ADAPT2: 2}
+
+STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ENOTBIJECTIVE",
+          4: "QS_ECUDA", 5: "QS_ETIMEOUT", 6: "QS_EZEROPROJ", 7: "QS_ENOTUNITARY",
+          8: "QS_EUNSUPPORTED"}
+
+
+class QSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class qs_gate(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int32), ("controls", ctypes.c_int32 * 2),
+                ("target", ctypes.c_int32), ("u", ctypes.c_double * 8)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "qs_last_error_string": (ctypes.c_char_p, []),
+    "qs_version": (ctypes.c_char_p, []),
+    "qs_kernel_launches": (ctypes.c_uint64, []),
+    "sim_create": (_I, [_I, _I, _P, ctypes.POINTER(_P)]),
+    "sim_create_in": (_I, [_I, _I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "sim_destroy": (_I, [_P]),
+    "sim_info": (_I, [_P, _IP, _IP, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
+    "sim_reset": (_I, [_P]),
+    "apply_gate": (_I, [_P, _I, _D]),
+    "apply_controlled": (_I, [_P, _IP, _I, _I, _D]),
+    "apply_fused": (_I, [_P, _IP, _I, _D]),
+    "apply_permutation": (_I, [_P, _IP, _I, _I, _I, ctypes.POINTER(ctypes.c_uint32)]),
+    "modmul_table": (_I, [ctypes.c_uint64, ctypes.c_uint64, _I, ctypes.POINTER(ctypes.c_uint32)]),
+    "shorbox_init": (_I, [_P, _I, ctypes.c_uint64, ctypes.c_uint64]),
+    "circuit_run": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP]),
+    "circuit_run_timed": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP, ctypes.POINTER(ctypes.c_float), _I]),
+    "gate_std": (_I, [ctypes.c_char_p, _IP, _I, _D, _I, ctypes.POINTER(qs_gate)]),
+    "sim_norm": (_I, [_P, _D]),
+    "expect_xyz": (_I, [_P, _D, _D, _D]),
+    "measure_probs": (_I, [_P, _IP, _I, _D]),
+    "sim_copy_out": (_I, [_P, _P, ctypes.c_size_t, _D]),
+    "sim_copy_in": (_I, [_P, _P, ctypes.c_size_t, _D]),
+    "sim_sync": (_I, [_P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _check(status):
+    if status != 0:
+        raise QSError(status, _lib.qs_last_error_string().decode())
+
+
+def _ints(xs):
+    xs = [int(x) for x in xs]
+    return (ctypes.c_int * max(1, len(xs)))(*xs), len(xs)
+
+
+def _dbl(xs):
+    a = np.ascontiguousarray(np.asarray(xs, dtype=np.float64).ravel())
+    return a, a.ctypes.data_as(_D)
+
+
+def version():
+    return _lib.qs_version().decode()
+
+
+def lib_path():
+    return LIB_PATH
+
+
+def kernel_launches():
+    """Number of CUDA kernels the library has launched in this process."""
+    return int(_lib.qs_kernel_launches())
+
+
+# ---------------------------------------------------------------------------
+# gate records
+# ---------------------------------------------------------------------------
+def gate_std(name, qubits, params=()):
+    """Mnemonic record (name, qubits, params) -> qs_gate via the library's
+    instruction-set table."""
+    g = qs_gate()
+    q, nq = _ints(qubits)
+    p, pp = _dbl(params if len(params) else [0.0])
+    _check(_lib.gate_std(name.encode(), q, nq, pp, len(params), ctypes.byref(g)))
+    return g
+
+
+def gate_array(records):
+    """Convert a list of gate records (no MODMUL) to a ctypes qs_gate array."""
+    arr = (qs_gate * max(1, len(records)))()
+    for i, (name, q, p) in enumerate(records):
+        arr[i] = gate_std(name, q, p)
+    return arr, len(records)
+
+
+def modmul_table(a, G, width):
+    t = np.empty(1 << width, dtype=np.uint32)
+    _check(_lib.modmul_table(int(a), int(G), int(width), t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return t
+
+
+# ---------------------------------------------------------------------------
+# simulator handle
+# ---------------------------------------------------------------------------
+class Sim:
+    """An N-qubit state on the current CUDA device.
+
+    enc: "c128", "c64" or "adapt2".  stream: a torch.cuda.Stream, a raw
+    cudaStream_t integer, or None for torch's current stream.  buffer: an
+    optional torch CUDA tensor whose storage holds the state (the library then
+    borrows it); by default torch allocates one.
+    """
+
+    def __init__(self, N, enc="c128", stream=None, buffer=None):
+        import torch
+        self.N = int(N)
+        self.enc = ENCODINGS[enc] if isinstance(enc, str) else int(enc)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream_handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        nbytes = AMP_BYTES[self.enc] << self.N
+        if buffer is None:
+            buffer = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        self._buf = buffer
+        ptr = buffer.data_ptr()
+        ptr_al = (ptr + 255) & ~255
+        avail = buffer.numel() * buffer.element_size() - (ptr_al - ptr)
+        h = _P()
+        _check(_lib.sim_create_in(self.N, self.enc, _P(ptr_al), avail, _P(self.stream_handle), ctypes.byref(h)))
+        self._h = h
+        self.nbytes = nbytes
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_lib.sim_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        _check(_lib.sim_reset(self._h))
+
+    def sync(self):
+        _check(_lib.sim_sync(self._h))
+
+    def device_ptr(self):
+        p = _P()
+        _check(_lib.sim_info(self._h, None, None, ctypes.byref(p), None))
+        return p.value
+
+    # -- gates --
+    def apply_gate(self, target, U):
+        u, up = _dbl(_mat8(U))
+        _check(_lib.apply_gate(self._h, int(target), up))
+
+    def apply_controlled(self, controls, target, U):
+        c, nc = _ints(controls)
+        u, up = _dbl(_mat8(U))
+        _check(_lib.apply_controlled(self._h, c, nc, int(target), up))
+
+    def apply_fused(self, qubits, U):
+        q, k = _ints(qubits)
+        U = np.asarray(U, dtype=np.complex128)
+        flat = np.empty(2 * U.size)
+        flat[0::2] = U.ravel().real
+        flat[1::2] = U.ravel().imag
+        f, fp = _dbl(flat)
+        _check(_lib.apply_fused(self._h, q, k, fp))
+
+    def apply_permutation(self, controls, reg_lo, reg_w, table):
+        c, nc = _ints(controls)
+        t = np.ascontiguousarray(np.asarray(table, dtype=np.uint32))
+        _check(_lib.apply_permutation(self._h, c, nc, int(reg_lo), int(reg_w),
+                                      t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+
+    def shorbox_init(self, nx, G, y):
+        _check(_lib.shorbox_init(self._h, int(nx), int(G), int(y)))
+
+    def circuit_run(self, gates, mode=1):
+        """gates: a ctypes qs_gate array (from gate_array) plus count, or a list
+        of records.  Returns the number of state sweeps launched."""
+        if isinstance(gates, tuple):
+            arr, n = gates
+        else:
+            arr, n = gate_array(gates)
+        npass = ctypes.c_int(0)
+        _check(_lib.circuit_run(self._h, arr, n, int(mode), ctypes.byref(npass)))
+        return npass.value
+
+    def circuit_run_timed(self, gates, mode=1, max_passes=4096):
+        """As circuit_run; returns the device time (ms) of every sweep."""
+        if isinstance(gates, tuple):
+            arr, n = gates
+        else:
+            arr, n = gate_array(gates)
+        npass = ctypes.c_int(0)
+        ms = (ctypes.c_float * max_passes)()
+        _check(_lib.circuit_run_timed(self._h, arr, n, int(mode), ctypes.byref(npass), ms, max_passes))
+        return [ms[i] for i in range(min(npass.value, max_passes))]
+
+    def run_records(self, records, mode=1):
+        """Run records in order; MODMUL records become a modmul table plus a
+        controlled permutation, runs of other records one circuit_run."""
+        run = []
+        passes = 0
+        for rec in records:
+            if rec[0] == "MODMUL":
+                if run:
+                    passes += self.circuit_run(run, mode)
+                    run = []
+                a, G, lo, w = rec[2]
+                self.apply_permutation(rec[1], lo, w, modmul_table(a, G, w))
+                passes += 1
+            else:
+                run.append(rec)
+        if run:
+            passes += self.circuit_run(run, mode)
+        return passes
+
+    # -- reductions --
+    def norm(self):
+        out = ctypes.c_double(0.0)
+        _check(_lib.sim_norm(self._h, ctypes.byref(out)))
+        return out.value
+
+    def expect_xyz(self):
+        qx = np.empty(self.N)
+        qy = np.empty(self.N)
+        qz = np.empty(self.N)
+        _check(_lib.expect_xyz(self._h, qx.ctypes.data_as(_D), qy.ctypes.data_as(_D), qz.ctypes.data_as(_D)))
+        return qx, qy, qz
+
+    def measure_probs(self, qubits):
+        q, nq = _ints(qubits)
+        out = np.empty(1 << nq)
+        _check(_lib.measure_probs(self._h, q, nq, out.ctypes.data_as(_D)))
+        return out
+
+    # -- raw access --
+    def copy_out(self):
+        """Raw amplitudes as numpy: complex128 / complex64 arrays, or
+        (uint16 words, (r0, r1)) for ADAPT2."""
+        r = np.zeros(2)
+        if self.enc == C128:
+            a = np.empty(1 << self.N, dtype=np.complex128)
+        elif self.enc == C64:
+            a = np.empty(1 << self.N, dtype=np.complex64)
+        else:
+            a = np.empty(1 << self.N, dtype=np.uint16)
+        _check(_lib.sim_copy_out(self._h, _P(a.ctypes.data), self.nbytes, r.ctypes.data_as(_D)))
+        return (a, (float(r[0]), float(r[1]))) if self.enc == ADAPT2 else a
+
+    def copy_in(self, a, r0r1=None):
+        if self.enc == C128:
+            a = np.ascontiguousarray(a, dtype=np.complex128)
+        elif self.enc == C64:
+            a = np.ascontiguousarray(a, dtype=np.complex64)
+        else:
+            a = np.ascontiguousarray(a, dtype=np.uint16)
+        if a.nbytes != self.nbytes:
+            raise ValueError("need %d bytes" % self.nbytes)
+        r = np.asarray(r0r1 if r0r1 is not None else (0.0, 0.0), dtype=np.float64)
+        _check(_lib.sim_copy_in(self._h, _P(a.ctypes.data), self.nbytes, r.ctypes.data_as(_D)))
+
+
+def _mat8(U):
+    U = np.asarray(U)
+    if U.shape == (8,):
+        return U.astype(np.float64)
+    U = U.astype(np.complex128).reshape(2, 2)
+    out = np.empty(8)
+    out[0::2] = U.ravel().real
+    out[1::2] = U.ravel().imag
+    return out
