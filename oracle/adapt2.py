@@ -21,8 +21,10 @@ Readings where the section is silent (each listed in the design notes):
   * r0 and r1 are re-tuned after every arithmetic gate from the post-gate
     values of the whole state (decode -> exact gate -> retune -> encode);
   * permutations (X, CNOT, TOFFOLI, modular multiplication) move codes
-    unchanged, and phase factors e^{i pi m/128} add m to b1 (mod 256): both
-    leave every |z| and hence r0, r1 unchanged;
+    unchanged, and phase factors e^{i pi m/128} add m to b1 (mod 256);
+    diagonal and anti-diagonal unitaries leave every |z| unchanged, so they
+    keep r0, r1 (re-tuning from decoded values would only move r1 by an
+    ulp of rounding);
   * the encoding does not renormalise.
 
 Word layout shared with the device state: one little-endian 16-bit word per
@@ -72,6 +74,31 @@ def encode(z, r0, r1):
     return b0.astype(np.int8), b1.astype(np.int8)
 
 
+def _angle_table():
+    """(cos, sin) of theta = pi b1 / 128 for b1 = -128..127 (index b1 + 128).
+
+    The values for 0 <= b1 < 64 are computed directly; the others follow by
+    exact quarter turns, (c, s) -> (-s, c), so that two amplitudes of equal
+    magnitude code and angles pi apart cancel exactly, as they do in exact
+    arithmetic."""
+    k = np.arange(64)
+    c = np.cos(PI * k / 128.0)
+    sn = np.sin(PI * k / 128.0)
+    cs = np.empty(256)
+    ss = np.empty(256)
+    for quarter in range(4):           # b1 = k + 64 * quarter - 128
+        idx = k + 64 * quarter
+        rc, rs = c, sn
+        for _ in range((quarter + 2) % 4):   # rotate by (quarter - 2) quarter turns
+            rc, rs = -rs, rc
+        cs[idx] = rc
+        ss[idx] = rs
+    return cs, ss
+
+
+ANGLE_COS, ANGLE_SIN = _angle_table()
+
+
 def decode(b0, b1, r0, r1):
     """Decode (b0, b1) codes with parameters (r0, r1) into complex128."""
     b0 = np.asarray(b0, dtype=np.int64)
@@ -79,8 +106,7 @@ def decode(b0, b1, r0, r1):
     r = (b0 + 127) * (r1 - r0) / 253.0 + r0
     r = np.where(b0 == -128, 0.0, r)
     r = np.where(b0 == 127, 1.0, r)
-    th = PI * b1 / 128.0
-    return r * np.cos(th) + 1j * (r * np.sin(th))
+    return r * ANGLE_COS[b1 + 128] + 1j * (r * ANGLE_SIN[b1 + 128])
 
 
 def pack(b0, b1):
@@ -127,10 +153,11 @@ class AState:
         return pack(self.b0, self.b1)
 
     # --- arithmetic gate: decode -> exact FP64 gate -> retune -> encode -----
-    def arithmetic(self, fn):
+    def arithmetic(self, fn, retune_range=True):
         z = self.to_complex()
         fn(z)
-        self.r0, self.r1 = retune(z)
+        if retune_range:
+            self.r0, self.r1 = retune(z)
         self.b0, self.b1 = encode(z, self.r0, self.r1)
         return self
 

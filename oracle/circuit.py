@@ -24,44 +24,62 @@ def run(v, N, records):
     return v
 
 
-def _pi128_steps(U):
-    """If U = diag(1, e^{i pi m/128}) exactly in angle (|u11| == 1 to 1e-15),
-    return m; else None."""
-    if U[0, 1] != 0 or U[1, 0] != 0 or U[0, 0] != 1:
+def _phase_m(f):
+    """m if the unit-modulus factor f equals e^{i pi m/128} (m integer), else None."""
+    if abs(abs(f) - 1.0) > 1e-15:
         return None
-    if abs(abs(U[1, 1]) - 1.0) > 1e-15:
-        return None
-    m = math.atan2(U[1, 1].imag, U[1, 1].real) * 128.0 / math.pi
+    m = math.atan2(f.imag, f.real) * 128.0 / math.pi
     mr = round(m)
-    if abs(m - mr) > 1e-9:
-        return None
-    return int(mr)
+    return int(mr) if abs(m - mr) <= 1e-9 else None
 
 
 def _is_permutation(U):
     return U[0, 0] == 0 and U[1, 1] == 0 and U[0, 1] == 1 and U[1, 0] == 1
 
 
+def _subspace(N, controls, target, bit):
+    i = np.arange(1 << N, dtype=np.int64)
+    on = ((i >> target) & 1) == bit
+    for c in controls:
+        on &= ((i >> c) & 1) == 1
+    return on
+
+
 def run_adapt2(a, records):
-    """Apply records to an adaptive-encoded state (Sec. 4.1).  X-type gates
-    (X, CNOT, TOFFOLI) move codes; diag(1, e^{i pi m/128}) phases (Z, S, T,
-    R(k<=8), U(k<=8), ...) add m to b1 where the controls and target are 1;
-    every other gate is decode -> exact gate -> retune -> encode."""
+    """Apply records to an adaptive-encoded state (Sec. 4.1).
+
+    X-type gates (X, CNOT, TOFFOLI) only move codes.  Diagonal and
+    anti-diagonal unitaries (Z, S, T, R, U(k), Y, RZ, ...) leave every |z|
+    unchanged, so r0 and r1 are kept: with phases e^{i pi m/128} the codes
+    move and b1 gains m; with other phases the state is decoded, multiplied
+    and re-encoded with the same (r0, r1).  Every other gate is
+    decode -> exact gate -> retune (r0, r1) -> encode."""
     N = a.N
     for rec in records:
         if rec[0].upper() == "I":
             continue
         controls, target, U = gates.as_controlled(rec)
+
+        def gate(x, controls=controls, target=target, U=U):
+            sv.apply_controlled_u2(x, N, controls, target, U)
+
         if _is_permutation(U):
-            a.permute(lambda x: sv.apply_controlled_u2(x, N, controls, target, U))
+            a.permute(gate)
             continue
-        m = _pi128_steps(U)
-        if m is not None:
-            i = np.arange(1 << N, dtype=np.int64)
-            on = ((i >> target) & 1) == 1
-            for c in controls:
-                on &= ((i >> c) & 1) == 1
-            a.phase_steps(np.where(on, m, 0))
+        diag = U[0, 1] == 0 and U[1, 0] == 0
+        anti = U[0, 0] == 0 and U[1, 1] == 0
+        if diag or anti:
+            f0, f1 = (U[0, 0], U[1, 1]) if diag else (U[0, 1], U[1, 0])
+            m0, m1 = _phase_m(f0), _phase_m(f1)
+            if m0 is not None and m1 is not None:
+                if anti:
+                    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+                    a.permute(lambda x: sv.apply_controlled_u2(x, N, controls, target, X))
+                steps = np.where(_subspace(N, controls, target, 0), m0, 0) + \
+                    np.where(_subspace(N, controls, target, 1), m1, 0)
+                a.phase_steps(steps)
+            else:
+                a.arithmetic(gate, retune_range=False)
             continue
-        a.arithmetic(lambda z: sv.apply_controlled_u2(z, N, controls, target, U))
+        a.arithmetic(gate)
     return a

@@ -52,13 +52,14 @@ static qs_status init_handle(qs_sim* s, int N, qs_encoding enc, void* stream) {
   s->N = N;
   s->enc = enc;
   s->stream = (cudaStream_t)stream;
-  s->r0 = s->r1 = 0.0;
+  s->a2dev = nullptr;
   s->scratch = nullptr;
   s->scratch_bytes = 0;
   s->hbuf = nullptr;
   s->hbuf_bytes = 0;
   QS_CUDA(cudaGetDevice(&s->device));
   QS_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
+  if (enc == QS_ADAPT2) QS_CUDA(cudaMalloc(&s->a2dev, sizeof(A2Dev)));
   return QS_OK;
 }
 
@@ -84,9 +85,10 @@ extern "C" qs_status sim_create(int N, qs_encoding enc, void* cuda_stream, qs_si
   qs_sim* s = new (std::nothrow) qs_sim;
   if (!s) return QS_ENOMEM;
   qs_status st = init_handle(s, N, enc, cuda_stream);
-  if (st != QS_OK) { delete s; return st; }
+  if (st != QS_OK) { if (s->a2dev) cudaFree(s->a2dev); delete s; return st; }
   cudaError_t e = cudaMalloc(&s->state, bytes);
   if (e != cudaSuccess) {
+    if (s->a2dev) cudaFree(s->a2dev);
     delete s;
     qs_set_error("sim_create: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     return QS_ENOMEM;
@@ -94,7 +96,7 @@ extern "C" qs_status sim_create(int N, qs_encoding enc, void* cuda_stream, qs_si
   s->bytes = bytes;
   s->owns = true;
   st = do_reset(s);
-  if (st != QS_OK) { cudaFree(s->state); delete s; return st; }
+  if (st != QS_OK) { cudaFree(s->state); if (s->a2dev) cudaFree(s->a2dev); delete s; return st; }
   *out = s;
   return QS_OK;
 }
@@ -113,12 +115,12 @@ extern "C" qs_status sim_create_in(int N, qs_encoding enc, void* dev_ptr, size_t
   qs_sim* s = new (std::nothrow) qs_sim;
   if (!s) return QS_ENOMEM;
   qs_status st = init_handle(s, N, enc, cuda_stream);
-  if (st != QS_OK) { delete s; return st; }
+  if (st != QS_OK) { if (s->a2dev) cudaFree(s->a2dev); delete s; return st; }
   s->state = dev_ptr;
   s->bytes = need;
   s->owns = false;
   st = do_reset(s);
-  if (st != QS_OK) { delete s; return st; }
+  if (st != QS_OK) { if (s->a2dev) cudaFree(s->a2dev); delete s; return st; }
   *out = s;
   return QS_OK;
 }
@@ -129,6 +131,7 @@ extern "C" qs_status sim_destroy(qs_sim* s) {
   if (s->scratch) cudaFree(s->scratch);
   if (s->hbuf) cudaFreeHost(s->hbuf);
   if (s->owns && s->state) cudaFree(s->state);
+  if (s->a2dev) cudaFree(s->a2dev);
   delete s;
   if (e != cudaSuccess) {
     qs_set_error("sim_destroy: %s", cudaGetErrorString(e));
@@ -276,39 +279,20 @@ static qs_status run_gates(qs_sim* s, const qs_gate* gates, int n, int mode, int
   CHECK_ARG(mode == 0 || mode == 1, "circuit_run: mode %d", mode);
   for (int i = 0; i < n; ++i) QS_TRY(check_gate(s, gates[i]));
   int passes = 0;
-  auto mark = [&](int k) -> qs_status {
-    if (ev && passes < max_ev) QS_CUDA(cudaEventRecord(ev[2 * passes + k], s->stream));
-    return QS_OK;
-  };
-  if (mode == 0 || s->enc == QS_ADAPT2) {
+  PassTimer timer = {ev, max_ev, 0};
+  if (mode == 0 || s->enc == QS_ADAPT2 || s->N < tile_bits(s->enc)) {
     for (int i = 0; i < n; ++i) {
       const qs_gate& g = gates[i];
       if (classify_u2(g.u).kind == GK_IDENT) continue;
-      QS_TRY(mark(0));
+      const bool timed = ev && timer.n < max_ev;
+      if (timed) QS_CUDA(cudaEventRecord(ev[2 * timer.n], s->stream));
       QS_TRY(apply_u2_checked(s, g.controls, g.nc, g.target, g.u));
-      QS_TRY(mark(1));
+      if (timed) QS_CUDA(cudaEventRecord(ev[2 * timer.n + 1], s->stream));
+      timer.n++;
       ++passes;
     }
   } else {
-    const int b = (s->enc == QS_C128) ? 12 : 13;
-    const int L = (s->enc == QS_C128) ? 5 : 6;
-    int bb = s->N < b ? s->N : b;
-    int LL = s->N < L ? s->N : L;
-    TilePass* tp = (TilePass*)malloc(sizeof(TilePass) * (size_t)(n + 1));
-    TileOp* ops = (TileOp*)malloc(sizeof(TileOp) * (size_t)(n + 1));
-    if (!tp || !ops) { free(tp); free(ops); return QS_ENOMEM; }
-    int np = plan_tile_passes(gates, n, s->N, bb, LL, tp, n + 1, ops, n + 1);
-    qs_status st = QS_OK;
-    for (int i = 0; i < np && st == QS_OK; ++i) {
-      if (tp[i].nops == 0) continue;
-      st = mark(0);
-      if (st == QS_OK) st = launch_tile_pass(s, tp[i], ops + tp[i].op_begin);
-      if (st == QS_OK) st = mark(1);
-      ++passes;
-    }
-    free(tp);
-    free(ops);
-    QS_TRY(st);
+    QS_TRY(run_tile_passes(s, gates, n, &passes, ev ? &timer : nullptr));
   }
   if (n_passes) *n_passes = passes;
   return QS_OK;
@@ -368,7 +352,7 @@ extern "C" qs_status sim_norm(qs_sim* s, double* out) {
 extern "C" qs_status expect_xyz(qs_sim* s, double* qx, double* qy, double* qz) {
   QS_TRY(check_sim(s));
   CHECK_ARG(qx && qy && qz, "expect_xyz: null output");
-  return (s->enc == QS_ADAPT2) ? a2_expect(s, qx, qy, qz) : launch_expect(s, qx, qy, qz);
+  return launch_expect(s, qx, qy, qz);
 }
 
 extern "C" qs_status measure_probs(qs_sim* s, const int* qubits, int nq, double* out) {
@@ -376,7 +360,7 @@ extern "C" qs_status measure_probs(qs_sim* s, const int* qubits, int nq, double*
   CHECK_ARG(nq >= 1 && nq <= 24 && nq <= s->N, "measure_probs: nq = %d not in 1..min(24, N)", nq);
   CHECK_ARG(out != nullptr, "measure_probs: null out");
   QS_TRY(check_qubits(s, qubits, nq, "measure_probs"));
-  return (s->enc == QS_ADAPT2) ? a2_marginal(s, qubits, nq, out) : launch_marginal(s, qubits, nq, out);
+  return launch_marginal(s, qubits, nq, out);
 }
 
 // ---- raw access --------------------------------------------------------------------------
@@ -385,7 +369,10 @@ extern "C" qs_status sim_copy_out(qs_sim* s, void* host, size_t bytes, double* r
   CHECK_ARG(host != nullptr && bytes == s->bytes, "sim_copy_out: need %zu bytes", s->bytes);
   QS_CUDA(cudaMemcpyAsync(host, s->state, bytes, cudaMemcpyDeviceToHost, s->stream));
   QS_CUDA(cudaStreamSynchronize(s->stream));
-  if (r0r1) { r0r1[0] = s->r0; r0r1[1] = s->r1; }
+  if (r0r1) {
+    r0r1[0] = r0r1[1] = 0.0;
+    if (s->enc == QS_ADAPT2) QS_TRY(a2_get_range(s, &r0r1[0], &r0r1[1]));
+  }
   return QS_OK;
 }
 
@@ -395,8 +382,7 @@ extern "C" qs_status sim_copy_in(qs_sim* s, const void* host, size_t bytes, cons
   if (s->enc == QS_ADAPT2) {
     CHECK_ARG(r0r1 != nullptr, "sim_copy_in: ADAPT2 needs (r0, r1)");
     CHECK_ARG(r0r1[0] >= 0 && r0r1[1] >= r0r1[0] && r0r1[1] < 1.0, "sim_copy_in: need 0 <= r0 <= r1 < 1");
-    s->r0 = r0r1[0];
-    s->r1 = r0r1[1];
+    QS_TRY(a2_set_range(s, r0r1[0], r0r1[1]));
   }
   QS_CUDA(cudaMemcpyAsync(s->state, host, bytes, cudaMemcpyHostToDevice, s->stream));
   QS_CUDA(cudaStreamSynchronize(s->stream));

@@ -15,7 +15,7 @@ struct qs_sim {
   void* state;        // device amplitudes
   size_t bytes;       // 2^N * bytes per amplitude
   bool owns;          // state allocated by the handle
-  double r0, r1;      // ADAPT2 magnitude range (Sec. 4.1)
+  void* a2dev;        // ADAPT2: device A2Dev block (current and next magnitude range)
   void* scratch;      // device scratch for reductions and ADAPT2 range passes
   size_t scratch_bytes;
   void* hbuf;         // pinned host staging for results
@@ -92,34 +92,35 @@ qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz);
 qs_status launch_marginal(qs_sim* s, const int* qubits, int nq, double* out);
 
 // Tile passes --------------------------------------------------------------------
-// One gate inside a shared-memory tile pass.
-struct TileOp {
-  int kind;            // GateKind; GK_DIAG with target outside the tile = "outer"
-  int c0, c1;          // unit codes
-  int p;               // local bit of the target (-1: target outside the tile)
-  uint32_t lmask;      // local control mask (bits of the tile index)
-  uint64_t gmask;      // outer control mask (global index bits, fixed per tile)
-  uint64_t gtbit;      // outer target bit (global), for outer diagonals
-  double u[8];
+// Optional per-launch timing: events ev[2i], ev[2i+1] around launch i.
+struct PassTimer {
+  cudaEvent_t* ev;
+  int max_ev;
+  int n;
 };
-struct TilePass {
-  int b;               // tile bits
-  int bits[16];        // global positions of the tile bits, ascending
-  int nops;
-  int op_begin;        // index into the op array
-};
-// Plan a gate list into tile passes (greedy, gate order preserved).
-int plan_tile_passes(const qs_gate* gates, int n, int N, int b, int low_bits,
-                     TilePass* passes, int max_passes, TileOp* ops, int max_ops);
-qs_status launch_tile_pass(qs_sim* s, const TilePass& pass, const TileOp* ops);
+// Number of tile bits used by the tile passes for an encoding.
+int tile_bits(qs_encoding enc);
+// Plan a gate list into tile passes and launch them (gate order preserved).
+qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer);
 
 // ADAPT2 --------------------------------------------------------------------------
+// Device-resident range of the adaptive encoding (Sec. 4.1): the current
+// (r0, r1) used to decode, and the min / max of |z| over 0 < |z| < 1 of the
+// post-gate values, gathered by the range pass (float bit patterns, atomics).
+struct A2Dev {
+  double r0, r1;
+  unsigned int mn, mx;
+  unsigned int pad[2];
+};
+qs_status a2_set_range(qs_sim* s, double r0, double r1);
+qs_status a2_get_range(qs_sim* s, double* r0, double* r1);
 qs_status a2_apply_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]);
 qs_status a2_norm(qs_sim* s, double* out);
-qs_status a2_expect(qs_sim* s, double* qx, double* qy, double* qz);
-qs_status a2_marginal(qs_sim* s, const int* qubits, int nq, double* out);
 qs_status a2_shorbox(qs_sim* s, int nx, uint64_t G, uint64_t y);
 qs_status a2_reset(qs_sim* s);
+
+// Fixed-order compensated sum of n device doubles into *out (device).
+qs_status sum_partials(qs_sim* s, const double* part, int n, double* out);
 
 // scratch management
 qs_status ensure_scratch(qs_sim* s, size_t bytes);

@@ -139,7 +139,8 @@ qs_status launch_shorbox(qs_sim* s, int nx, uint64_t G, uint64_t y) {
     // every nonzero amplitude has |z| = 2^{-nx/2} = r0 = r1: b0 = -127, b1 = 0
     k_shorbox<uint16_t><<<blocks, TPB, 0, s->stream>>>((uint16_t*)s->state, nx, F, G, y,
                                                         (uint16_t)0x0081, (uint16_t)0x0080);
-    s->r0 = s->r1 = amp;
+    QS_LAUNCH_CHECK();
+    return a2_set_range(s, amp, amp);
   }
   QS_LAUNCH_CHECK();
   return QS_OK;
@@ -155,7 +156,8 @@ qs_status launch_reset(qs_sim* s) {
   } else {
     // b0 = -128 (r = 0) everywhere, b0 = 127 (r = 1) at index 0; r0 = r1 = 0
     k_fill<uint16_t><<<blocks, TPB, 0, s->stream>>>((uint16_t*)s->state, n, (uint16_t)0x0080, (uint16_t)0x007F);
-    s->r0 = s->r1 = 0.0;
+    QS_LAUNCH_CHECK();
+    return a2_set_range(s, 0.0, 0.0);
   }
   QS_LAUNCH_CHECK();
   return QS_OK;

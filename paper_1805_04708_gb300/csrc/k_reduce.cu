@@ -9,6 +9,7 @@
 // before being folded into FP64, which keeps the work on the FP32 pipes.
 #include "internal.cuh"
 #include "cplx.cuh"
+#include "a2codec.cuh"
 #include <string.h>
 
 namespace {
@@ -30,12 +31,6 @@ __device__ __forceinline__ void ff_add_prod(FF& s, float a, float b) {
   float e = fmaf(a, b, -p);
   ff_add(s, p);
   s.lo += e;
-}
-__device__ __forceinline__ void ff_sub_prod(FF& s, float a, float b) {
-  float p = a * b;
-  float e = fmaf(a, b, -p);
-  ff_add(s, -p);
-  s.lo -= e;
 }
 __device__ __forceinline__ double ff_val(const FF& s) { return (double)s.hi + (double)s.lo; }
 
@@ -74,15 +69,31 @@ __global__ void __launch_bounds__(TPB) k_norm_c128(const double2* __restrict__ s
 __global__ void __launch_bounds__(TPB) k_norm_c64(const float4* __restrict__ s, uint64_t n, double* part) {
   __shared__ double sh[32];
   double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * TPB;
+  uint64_t i = (uint64_t)blockIdx.x * TPB + threadIdx.x;
+  // four independent loads in flight per thread; products exact (p + e),
+  // summed in float-float, folded into FP64 every iteration
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    float4 a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = s[i + u * stride];
+    FF f = {0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ff_add_prod(f, a[u].x, a[u].x);
+      ff_add_prod(f, a[u].y, a[u].y);
+      ff_add_prod(f, a[u].z, a[u].z);
+      ff_add_prod(f, a[u].w, a[u].w);
+    }
+    acc += ff_val(f);
+  }
   FF f = {0.f, 0.f};
-  int cnt = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
+  for (; i < n; i += stride) {
     float4 a = s[i];
     ff_add_prod(f, a.x, a.x);
     ff_add_prod(f, a.y, a.y);
     ff_add_prod(f, a.z, a.z);
     ff_add_prod(f, a.w, a.w);
-    if (++cnt == 8) { acc += ff_val(f); f.hi = f.lo = 0.f; cnt = 0; }
   }
   acc += ff_val(f);
   double r = block_sum(acc, sh);
@@ -117,19 +128,6 @@ __global__ void k_sum_columns(const double* __restrict__ part, int rows, int col
   if (threadIdx.x == 0) out[c] = shs[0] + shc[0];
 }
 
-// ---- expect_xyz tile passes -------------------------------------------------------------
-// A tile is the 2^b amplitudes whose index bits outside `bits` are fixed:
-// bits[0..L-1] are the low L index bits (contiguous runs of 2^L amplitudes),
-// bits[L..b-1] are higher bits.  For the local bits p >= p_new the pass
-// accumulates, per tile, Re/Im of sum conj(a(l)) a(l | 2^p) over l with bit
-// p = 0, and P(bit = 1); pass 0 also accumulates the total |a|^2.
-struct TileGeo {
-  int N, b, L, p_new;
-  uint64_t hi_mask;        // global mask of bits[L..b-1]
-  uint64_t out_mask;       // global mask of the bits outside the tile
-  int hb[16];              // global positions of bits[L..b-1]
-};
-
 __device__ __forceinline__ uint64_t deposit(uint64_t x, uint64_t mask) {
   uint64_t r = 0;
   for (uint64_t m = mask; m; m &= m - 1) {
@@ -138,91 +136,265 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, uint64_t mask) {
   }
   return r;
 }
-
-template <typename A> struct ElemT;
-template <> struct ElemT<double2> { using R = double; };
-template <> struct ElemT<float2> { using R = float; };
-
-// per-pair accumulation: re += Re(conj(a0) a1), im += Im(conj(a0) a1), p1 += |a1|^2
-struct AccD {
-  double re, im, p1;
-  __device__ void zero() { re = im = p1 = 0.0; }
-  __device__ void add(double2 a0, double2 a1) {
-    re = fma(a0.x, a1.x, re); re = fma(a0.y, a1.y, re);
-    im = fma(a0.x, a1.y, im); im = fma(-a0.y, a1.x, im);
-    p1 = fma(a1.x, a1.x, p1); p1 = fma(a1.y, a1.y, p1);
-  }
-  __device__ double vre() const { return re; }
-  __device__ double vim() const { return im; }
-  __device__ double vp1() const { return p1; }
-};
-struct AccF {
-  FF re, im, p1;
-  __device__ void zero() { re.hi = re.lo = im.hi = im.lo = p1.hi = p1.lo = 0.f; }
-  __device__ void add(float2 a0, float2 a1) {
-    ff_add_prod(re, a0.x, a1.x); ff_add_prod(re, a0.y, a1.y);
-    ff_add_prod(im, a0.x, a1.y); ff_sub_prod(im, a0.y, a1.x);
-    ff_add_prod(p1, a1.x, a1.x); ff_add_prod(p1, a1.y, a1.y);
-  }
-  __device__ double vre() const { return ff_val(re); }
-  __device__ double vim() const { return ff_val(im); }
-  __device__ double vp1() const { return ff_val(p1); }
-};
-template <typename A> struct AccT;
-template <> struct AccT<double2> { using T = AccD; };
-template <> struct AccT<float2> { using T = AccF; };
-
 __device__ __forceinline__ double sq(double2 a) { return a.x * a.x + a.y * a.y; }
 __device__ __forceinline__ double sq(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
 
-// partials layout per block: [ (b - p_new) * 3 + 1 ] doubles
+// ---- expect_xyz for small states (N <= 12): one CTA, FP64 throughout -------------------
 template <typename A>
-__global__ void __launch_bounds__(TPB) k_expect_tiles(const A* __restrict__ s, TileGeo g, double* part) {
-  extern __shared__ unsigned char smraw[];
-  A* tile = (A*)smraw;
-  const int nb = g.b - g.p_new;
-  double* wacc = (double*)(smraw + ((size_t)sizeof(A) << g.b));  // [warps][nb*3+1]
-  const int nw = TPB / 32, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int stride = nb * 3 + 1;
-  for (int i = threadIdx.x; i < nw * stride; i += TPB) wacc[i] = 0.0;
-  const uint64_t ntiles = 1ull << (g.N - g.b);
-  const int tsize = 1 << g.b;
-  const int lmask = (1 << g.L) - 1;
+__device__ __forceinline__ double2 to_d2(const A& a, const Luts& L) { return make_double2((double)a.x, (double)a.y); }
+template <>
+__device__ __forceinline__ double2 to_d2<uint16_t>(const uint16_t& w, const Luts& L) {
+  Cx<float> z = a2_dec(L, w);
+  return make_double2((double)z.x, (double)z.y);
+}
+template <typename A>
+__global__ void __launch_bounds__(TPB) k_expect_small(const A* __restrict__ s, int N, double* out, const A2Dev* a2) {
+  __shared__ double2 t[4096];
+  __shared__ double sh[32];
+  __shared__ Luts L;
+  if (a2) build_luts(L, a2->r0, a2->r1);
+  const int n = 1 << N;
+  for (int i = threadIdx.x; i < n; i += TPB) t[i] = to_d2<A>(s[i], L);
   __syncthreads();
   double tot = 0.0;
-  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
-    const uint64_t base = deposit(tau, g.out_mask);
-    for (int l = threadIdx.x; l < tsize; l += TPB) {
-      uint64_t h = (uint64_t)(l >> g.L);
-      uint64_t gi = base | (uint64_t)(l & lmask);
-      for (int k = 0; k < g.b - g.L; ++k) gi |= ((h >> k) & 1ull) << g.hb[k];
-      tile[l] = s[gi];
+  for (int i = threadIdx.x; i < n; i += TPB) tot += t[i].x * t[i].x + t[i].y * t[i].y;
+  tot = block_sum(tot, sh);
+  if (threadIdx.x == 0) out[0] = tot;
+  for (int q = 0; q < N; ++q) {
+    double re = 0.0, im = 0.0, p1 = 0.0;
+    for (int j = threadIdx.x; j < n / 2; j += TPB) {
+      const int l0 = (int)ins0((uint64_t)j, q), l1 = l0 | (1 << q);
+      const double2 a = t[l0], b = t[l1];
+      re += a.x * b.x + a.y * b.y;
+      im += a.x * b.y - a.y * b.x;
+      p1 += b.x * b.x + b.y * b.y;
     }
+    re = block_sum(re, sh);
     __syncthreads();
-    if (g.p_new == 0)
-      for (int l = threadIdx.x; l < tsize; l += TPB) tot += sq(tile[l]);
-    for (int p = g.p_new; p < g.b; ++p) {
-      typename AccT<A>::T acc;
-      acc.zero();
-      for (int j = threadIdx.x; j < (tsize >> 1); j += TPB) {
-        int l0 = (int)ins0((uint64_t)j, p);
-        acc.add(tile[l0], tile[l0 | (1 << p)]);
+    im = block_sum(im, sh);
+    __syncthreads();
+    p1 = block_sum(p1, sh);
+    __syncthreads();
+    if (threadIdx.x == 0) { out[1 + 3 * q] = re; out[2 + 3 * q] = im; out[3 + 3 * q] = p1; }
+  }
+}
+
+// ---- expect_xyz: register-tile passes -----------------------------------------------------
+// A pass reads the state once in tiles of 2^(RB+8) amplitudes: inside a CTA of
+// 256 threads, local bit 0 and RB-1 chosen qubits are register slots (each
+// thread holds 2^RB amplitudes), index bits 1..5 are the 32 lanes, and 3 more
+// qubits are the 8 warps.  For a register-slot qubit n the pairs
+// (a(*0_n*), a(*1_n*)) sit in one thread's registers; for a lane qubit the
+// partner comes by a warp shuffle.  Pass 0 computes w_n for qubit 0, the lane
+// qubits 1..5 and its slot qubits, plus sum |a|^2 per register slot and lane
+// bit and per tile and warp (from which P_n(1) of every qubit follows); later
+// passes compute w_n for RB-1 new slot qubits each.
+//
+// Per-thread sums are formed per tile in the arithmetic type (FP32 for
+// complex64, FP64 for complex128) and folded into per-thread accumulators in
+// shared memory (float-float / FP64), then reduced over the CTA and the grid
+// in a fixed order.
+constexpr int ETPB = 256;
+
+struct RedParams {
+  int N, RB;
+  int first;                 // pass 0
+  int nslots_new;            // slots 1..nslots_new carry new qubits (pass 0: also slot 0)
+  uint8_t slot_g[8];         // global qubit of slot s (slot_g[0] = 0)
+  uint8_t warp_g[3];         // global qubit of warp bit k
+  uint64_t out_mask;         // global bits outside the tile
+};
+
+template <typename R> struct SAcc;
+template <> struct SAcc<float> {
+  // float-float accumulators, [acc][thread] in shared memory
+  float* hi; float* lo;
+  __device__ void init(unsigned char* base, int nacc) {
+    hi = (float*)base; lo = hi + nacc * ETPB;
+    for (int i = 0; i < nacc; ++i) { hi[i * ETPB + threadIdx.x] = 0.f; lo[i * ETPB + threadIdx.x] = 0.f; }
+  }
+  __device__ __forceinline__ void add(int i, float x) {
+    FF f = {hi[i * ETPB + threadIdx.x], lo[i * ETPB + threadIdx.x]};
+    ff_add(f, x);
+    hi[i * ETPB + threadIdx.x] = f.hi; lo[i * ETPB + threadIdx.x] = f.lo;
+  }
+  __device__ double get(int i) const { return (double)hi[i * ETPB + threadIdx.x] + (double)lo[i * ETPB + threadIdx.x]; }
+  __host__ __device__ static size_t bytes(int nacc) { return (size_t)nacc * ETPB * 8; }
+};
+template <> struct SAcc<double> {
+  double* a;
+  __device__ void init(unsigned char* base, int nacc) {
+    a = (double*)base;
+    for (int i = 0; i < nacc; ++i) a[i * ETPB + threadIdx.x] = 0.0;
+  }
+  __device__ __forceinline__ void add(int i, double x) { a[i * ETPB + threadIdx.x] += x; }
+  __device__ double get(int i) const { return a[i * ETPB + threadIdx.x]; }
+  __host__ __device__ static size_t bytes(int nacc) { return (size_t)nacc * ETPB * 8; }
+};
+
+template <typename R> __device__ __forceinline__ R shfx(R x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+
+// sum over pairs (j, j | 2^S) of conj(v[j]) v[j | 2^S]
+template <typename R, int RB, int S>
+__device__ __forceinline__ void slot_w(const Cx<R>* v, R& re, R& im) {
+  re = 0; im = 0;
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    if ((j >> S) & 1) continue;
+    const Cx<R> a = v[j], b = v[j | (1 << S)];
+    re = fma(a.x, b.x, re); re = fma(a.y, b.y, re);
+    im = fma(a.x, b.y, im); im = fma(-a.y, b.x, im);
+  }
+}
+template <typename R, int RB>
+__device__ __forceinline__ void slot_w_rt(const Cx<R>* v, int s, R& re, R& im) {
+  switch (s) {
+    case 0: slot_w<R, RB, 0>(v, re, im); break;
+    case 1: slot_w<R, RB, 1>(v, re, im); break;
+    case 2: slot_w<R, RB, 2>(v, re, im); break;
+    case 3: slot_w<R, RB, 3>(v, re, im); break;
+    default: slot_w<R, RB, (RB > 4 ? 4 : 3)>(v, re, im); break;
+  }
+}
+
+// ENC: 0 complex64, 1 complex128, 2 adaptive 2-byte words (decoded to FP32)
+template <typename R, int RB, int ENC>
+__global__ void __launch_bounds__(ETPB, 2) k_expect2(const void* __restrict__ s, const __grid_constant__ RedParams P,
+                                                      double* __restrict__ tile_tot, double* __restrict__ part,
+                                                      const A2Dev* __restrict__ a2) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ Luts L;
+  if (ENC == 2) build_luts(L, a2->r0, a2->r1);
+  constexpr int NR = 1 << RB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // accumulators: pass 0: [w re/im: slot 0, lanes 0..4, slots 1..ns] [P1: slots 0..RB-1, lanes 0..4]
+  //               later : [w re/im: slots 1..ns]
+  const int nw = P.first ? (1 + 5 + P.nslots_new) : P.nslots_new;
+  const int nacc = 2 * nw + (P.first ? (RB + 5) : 0);
+  uint64_t* roff = (uint64_t*)smraw;                    // NR/2 register-pair offsets
+  SAcc<R> acc;
+  acc.init(smraw + 256, nacc);
+  if (threadIdx.x < NR / 2) {
+    uint64_t g = 0;
+    for (int sl = 1; sl < RB; ++sl)
+      if (((2 * threadIdx.x) >> sl) & 1) g |= 1ull << P.slot_g[sl];
+    roff[threadIdx.x] = g;
+  }
+  uint64_t woff = ((uint64_t)lane << 1);
+  for (int k = 0; k < 3; ++k)
+    if ((warp >> k) & 1) woff |= 1ull << P.warp_g[k];
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (P.N - RB - 8);
+  Cx<R> v[NR];
+  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+    const uint64_t base = deposit(tau, P.out_mask) | woff;
+    if constexpr (ENC == 2) {
+      const unsigned int* s2 = (const unsigned int*)s;
+#pragma unroll
+      for (int jj = 0; jj < NR / 2; ++jj) {
+        const unsigned int w = s2[(base + roff[jj]) >> 1];
+        v[2 * jj] = a2_dec(L, w & 0xFFFFu);
+        v[2 * jj + 1] = a2_dec(L, w >> 16);
       }
-      double re = warp_sum(acc.vre()), im = warp_sum(acc.vim()), p1 = warp_sum(acc.vp1());
-      if (lane == 0) {
-        double* d = wacc + w * stride + (p - g.p_new) * 3;
-        d[0] += re; d[1] += im; d[2] += p1;
+    } else if constexpr (sizeof(R) == 4) {
+      const float4* s4 = (const float4*)s;
+#pragma unroll
+      for (int jj = 0; jj < NR / 2; ++jj) {
+        float4 x = s4[(base + roff[jj]) >> 1];
+        v[2 * jj] = cx<float>(x.x, x.y);
+        v[2 * jj + 1] = cx<float>(x.z, x.w);
       }
+    } else {
+      const double2* s2 = (const double2*)s;
+#pragma unroll
+      for (int jj = 0; jj < NR / 2; ++jj) {
+        double2 x = s2[base + roff[jj]], y = s2[base + roff[jj] + 1];
+        v[2 * jj] = cx<double>(x.x, x.y);
+        v[2 * jj + 1] = cx<double>(y.x, y.y);
+      }
+    }
+    int ai = 0;
+    if (P.first) {
+      R re, im;
+      slot_w<R, RB, 0>(v, re, im);
+      acc.add(ai++, re); acc.add(ai++, im);
+      for (int k = 0; k < 5; ++k) {
+        const int m = 1 << k;
+        const bool lo = !((lane >> k) & 1);
+        R r2 = 0, i2 = 0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          const R px = shfx<R>(v[j].x, m), py = shfx<R>(v[j].y, m);
+          r2 = fma(v[j].x, px, r2); r2 = fma(v[j].y, py, r2);
+          i2 = fma(v[j].x, py, i2); i2 = fma(-v[j].y, px, i2);
+        }
+        acc.add(ai++, lo ? r2 : (R)0); acc.add(ai++, lo ? i2 : (R)0);
+      }
+    }
+    for (int sl = 1; sl <= P.nslots_new; ++sl) {
+      R re, im;
+      slot_w_rt<R, RB>(v, sl, re, im);
+      acc.add(ai++, re); acc.add(ai++, im);
+    }
+    if (P.first) {
+      R p[NR];
+      R T = 0;
+#pragma unroll
+      for (int j = 0; j < NR; ++j) { p[j] = fma(v[j].x, v[j].x, v[j].y * v[j].y); T += p[j]; }
+#pragma unroll
+      for (int sl = 0; sl < RB; ++sl) {
+        R q = 0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+          if ((j >> sl) & 1) q += p[j];
+        acc.add(ai++, q);
+      }
+      for (int k = 0; k < 5; ++k) acc.add(ai++, ((lane >> k) & 1) ? T : (R)0);
+      double t = warp_sum((double)T);
+      if (lane == 0) tile_tot[tau * 8 + warp] = t;
+    }
+  }
+  // CTA reduction of every accumulator in a fixed order
+  __syncthreads();
+  double* red = (double*)(smraw + 256 + SAcc<R>::bytes(nacc));   // [8 warps]
+  for (int i = 0; i < nacc; ++i) {
+    double x = warp_sum(acc.get(i));
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < ETPB / 32; ++w) t += red[w];
+      part[(size_t)blockIdx.x * nacc + i] = t;
     }
     __syncthreads();
   }
-  tot = warp_sum(tot);
-  if (lane == 0) wacc[w * stride + nb * 3] += tot;
-  __syncthreads();
-  for (int i = threadIdx.x; i < stride; i += TPB) {
-    double r = 0.0;
-    for (int ww = 0; ww < nw; ++ww) r += wacc[ww * stride + i];
-    part[(size_t)blockIdx.x * stride + i] = r;
+}
+
+// P1 of the warp and outer qubits from the per-(tile, warp) totals: one
+// column per qubit (col 0 = total), rows = CTAs of a grid-stride sum.
+__global__ void k_tile_bits(const double* __restrict__ tile_tot, uint64_t ntiles, RedParams P, int nq_out,
+                            const uint8_t* __restrict__ qlist, double* __restrict__ part) {
+  // thread handles (tile, warp) entries in a grid-stride loop; per-thread sums
+  // for the total and for each listed qubit (<= 40)
+  double acc[41];
+  for (int i = 0; i <= nq_out; ++i) acc[i] = 0.0;
+  const uint64_t n = ntiles * 8;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t tau = e >> 3;
+    const int w = (int)(e & 7);
+    uint64_t g = deposit(tau, P.out_mask);
+    for (int k = 0; k < 3; ++k)
+      if ((w >> k) & 1) g |= 1ull << P.warp_g[k];
+    const double x = tile_tot[e];
+    acc[0] += x;
+    for (int i = 0; i < nq_out; ++i)
+      if ((g >> qlist[i]) & 1) acc[i + 1] += x;
+  }
+  __shared__ double sh[32];
+  for (int i = 0; i <= nq_out; ++i) {
+    double r = block_sum(acc[i], sh);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * (nq_out + 1) + i] = r;
+    __syncthreads();
   }
 }
 
@@ -239,7 +411,16 @@ struct MargGeo {
 };
 
 template <typename A>
-__global__ void __launch_bounds__(TPB) k_marginal(const A* __restrict__ s, MargGeo g, double* part) {
+__device__ __forceinline__ double sqa(const A& a, const float* r) { return sq(a); }
+template <>
+__device__ __forceinline__ double sqa<uint16_t>(const uint16_t& w, const float* r) {
+  const double m = (double)r[(w & 0xFFu) ^ 0x80u];
+  return m * m;
+}
+template <typename A>
+__global__ void __launch_bounds__(TPB) k_marginal(const A* __restrict__ s, MargGeo g, double* part, const A2Dev* a2) {
+  __shared__ Luts L;
+  if (a2) build_luts(L, a2->r0, a2->r1);
   const uint64_t R = 1ull << g.nq;
   const uint64_t tid = (uint64_t)blockIdx.x * TPB + threadIdx.x;
   if (tid >= (R << g.nseg_log)) return;
@@ -255,7 +436,7 @@ __global__ void __launch_bounds__(TPB) k_marginal(const A* __restrict__ s, MargG
   uint64_t x = deposit(seg * g.seglen, g.cmask);
   double acc = 0.0;
   for (uint64_t j = 0; j < g.seglen; ++j) {
-    acc += sq(s[ireg | x]);
+    acc += sqa<A>(s[ireg | x], L.r);
     x = (x - g.cmask) & g.cmask;  // next subset of cmask in increasing order
   }
   part[seg * R + kout] = acc;
@@ -286,7 +467,7 @@ qs_status ensure_hbuf(qs_sim* s, size_t bytes) {
   return QS_OK;
 }
 
-static int reduce_grid(qs_sim* s) { return s->num_sms * 4; }
+static int reduce_grid(qs_sim* s) { return s->num_sms * 8; }
 
 qs_status launch_norm(qs_sim* s, double* out) {
   const int G = reduce_grid(s);
@@ -309,83 +490,130 @@ qs_status launch_norm(qs_sim* s, double* out) {
   return QS_OK;
 }
 
-template <typename A>
+template <typename R, int RB, int ENC>
 static qs_status expect_impl(qs_sim* s, double* qx, double* qy, double* qz) {
   const int N = s->N;
-  const int bmax = (sizeof(A) == 16) ? 12 : 13;
-  const int b0 = N < bmax ? N : bmax;
-  const int L = N < 5 ? N : 5;
-  // pass list: pass 0 covers bits 0..b0-1; then groups of (bmax - L) bits.
-  struct P { int b, p_new, first_new; };
-  P passes[64];
+  const int b = RB + 8;
+  if (N < b) return QS_EUNSUPPORTED;  // small states use the generic path
+  const int G = s->num_sms * 2;
+  const uint64_t ntiles = 1ull << (N - b);
+  const int grid = (int)(ntiles < (uint64_t)G ? ntiles : (uint64_t)G);
+  // pass list: pass 0 = qubits 0..5 (slot 0 + lanes) + slots 1..RB-1 = qubits 6..RB+4,
+  // warps = the next 3 qubits; later passes take RB-1 new qubits as slots.
+  struct Pass { RedParams P; int qs[8]; };
+  Pass passes[32];
   int np = 0;
-  passes[np++] = {b0, 0, 0};
-  for (int q = b0; q < N;) {
-    int gsz = bmax - L;
-    if (q + gsz > N) gsz = N - q;
-    passes[np++] = {L + gsz, L, q};
-    q += gsz;
+  int next = 6;
+  while (next < N || np == 0) {
+    Pass& ps = passes[np];
+    memset(&ps, 0, sizeof ps);
+    RedParams& P = ps.P;
+    P.N = N; P.RB = RB; P.first = (np == 0);
+    uint64_t tmask = 63ull;
+    P.slot_g[0] = 0;
+    int ns = 0;
+    for (int sl = 1; sl < RB && next < N; ++sl) { P.slot_g[sl] = (uint8_t)next; tmask |= 1ull << next; ps.qs[ns++] = next++; }
+    P.nslots_new = ns;
+    // fill the remaining slots and the warp bits with unused qubits (not new)
+    int fill = 6;
+    auto take = [&]() { while ((tmask >> fill) & 1) ++fill; tmask |= 1ull << fill; return fill; };
+    for (int sl = ns + 1; sl < RB; ++sl) P.slot_g[sl] = (uint8_t)take();
+    for (int k = 0; k < 3; ++k) P.warp_g[k] = (uint8_t)take();
+    const uint64_t all = (N >= 64) ? ~0ull : ((1ull << N) - 1);
+    P.out_mask = all & ~tmask;
+    ++np;
   }
-  const int G = reduce_grid(s);
-  size_t need = 0;
-  for (int i = 0; i < np; ++i) need += (size_t)G * ((passes[i].b - passes[i].p_new) * 3 + 1) + 64;
-  QS_TRY(ensure_scratch(s, need * sizeof(double) + 3 * 64 * sizeof(double)));
-  double* part = (double*)s->scratch;
-  double* res = part;  // per pass results follow the partials
+  // scratch: per pass partials, tile totals, column results
+  const int nacc0 = 2 * (1 + 5 + passes[0].P.nslots_new) + RB + 5;
+  const int nq_out = N - 6 - (RB - 1) >= 0 ? (3 + (N - b)) : 0;
   size_t off = 0;
-  size_t res_off[64];
-  int stride_of[64];
+  size_t part_off[32], res_off[32];
+  int nacc_of[32];
   for (int i = 0; i < np; ++i) {
-    const P& p = passes[i];
-    TileGeo g;
-    g.N = N; g.b = p.b; g.L = (i == 0) ? p.b : L; g.p_new = p.p_new;
-    g.hi_mask = 0;
-    uint64_t tmask = 0;
-    if (i == 0) {
-      tmask = (p.b >= 64) ? ~0ull : ((1ull << p.b) - 1);
-    } else {
-      tmask = (1ull << L) - 1;
-      for (int k = 0; k < p.b - L; ++k) { g.hb[k] = p.first_new + k; g.hi_mask |= 1ull << (p.first_new + k); }
-      tmask |= g.hi_mask;
-    }
-    g.out_mask = ((N >= 64) ? ~0ull : ((1ull << N) - 1)) & ~tmask;
-    const uint64_t ntiles = 1ull << (N - p.b);
-    int grid = (int)((ntiles < (uint64_t)G) ? ntiles : (uint64_t)G);
-    const int stride = (p.b - p.p_new) * 3 + 1;
-    size_t smem = ((size_t)sizeof(A) << p.b) + (TPB / 32) * stride * sizeof(double);
-    QS_CUDA(cudaFuncSetAttribute(k_expect_tiles<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_expect_tiles<A><<<grid, TPB, smem, s->stream>>>((const A*)s->state, g, part + off);
-    QS_LAUNCH_CHECK();
-    res_off[i] = off + (size_t)grid * stride;
-    stride_of[i] = stride;
-    k_sum_columns<<<stride, TPB, 0, s->stream>>>(part + off, grid, stride, part + res_off[i]);
-    QS_LAUNCH_CHECK();
-    off = res_off[i] + stride;
+    nacc_of[i] = (i == 0) ? nacc0 : 2 * passes[i].P.nslots_new;
+    part_off[i] = off; off += (size_t)grid * nacc_of[i];
+    res_off[i] = off; off += nacc_of[i];
   }
+  const size_t tt_off = off; off += ntiles * 8;
+  const int gtb = 64;
+  const size_t tbp_off = off; off += (size_t)gtb * (nq_out + 1);
+  const size_t tbr_off = off; off += nq_out + 1;
+  const size_t ql_off = off; off += 8;   // 64 bytes of qubit list
+  QS_TRY(ensure_scratch(s, off * sizeof(double)));
+  double* sc = (double*)s->scratch;
+  // warp + outer qubits of pass 0, in the order used by k_tile_bits
+  uint8_t ql[64];
+  int nql = 0;
+  {
+    const RedParams& P0 = passes[0].P;
+    for (int k = 0; k < 3; ++k) ql[nql++] = P0.warp_g[k];
+    for (int q = 0; q < N; ++q)
+      if ((P0.out_mask >> q) & 1) ql[nql++] = (uint8_t)q;
+  }
+  QS_CUDA(cudaMemcpyAsync(sc + ql_off, ql, 64, cudaMemcpyHostToDevice, s->stream));
+  for (int i = 0; i < np; ++i) {
+    const size_t smem = 256 + SAcc<R>::bytes(nacc_of[i]) + 8 * sizeof(double);
+    QS_CUDA(cudaFuncSetAttribute(k_expect2<R, RB, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_expect2<R, RB, ENC><<<grid, ETPB, smem, s->stream>>>(s->state, passes[i].P, sc + tt_off, sc + part_off[i],
+                                                           (const A2Dev*)s->a2dev);
+    QS_LAUNCH_CHECK();
+    k_sum_columns<<<nacc_of[i], TPB, 0, s->stream>>>(sc + part_off[i], grid, nacc_of[i], sc + res_off[i]);
+    QS_LAUNCH_CHECK();
+  }
+  k_tile_bits<<<gtb, TPB, 0, s->stream>>>(sc + tt_off, ntiles, passes[0].P, nql, (const uint8_t*)(sc + ql_off),
+                                          sc + tbp_off);
+  QS_LAUNCH_CHECK();
+  k_sum_columns<<<nql + 1, TPB, 0, s->stream>>>(sc + tbp_off, gtb, nql + 1, sc + tbr_off);
+  QS_LAUNCH_CHECK();
   QS_TRY(ensure_hbuf(s, off * sizeof(double)));
-  QS_CUDA(cudaMemcpyAsync(s->hbuf, part, off * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(cudaMemcpyAsync(s->hbuf, sc, off * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   QS_CUDA(cudaStreamSynchronize(s->stream));
   const double* h = (const double*)s->hbuf;
-  (void)res;
-  double nrm = h[res_off[0] + (passes[0].b - passes[0].p_new) * 3];
-  for (int i = 0; i < np; ++i) {
+  const double* t = h + tbr_off;
+  const double nrm = t[0];
+  for (int i = 0; i < nql; ++i) qz[ql[i]] = t[i + 1];
+  const double* r0 = h + res_off[0];
+  const RedParams& P0 = passes[0].P;
+  // pass 0 layout: w(slot 0), w(lanes 0..4), w(slots 1..ns), P1(slots 0..RB-1), P1(lanes 0..4)
+  int ai = 0;
+  auto setw = [&](int q, const double* r) { qx[q] = 0.5 * nrm - r[0]; qy[q] = 0.5 * nrm - r[1]; };
+  setw(0, r0 + ai); ai += 2;
+  for (int k = 0; k < 5; ++k) { setw(k + 1, r0 + ai); ai += 2; }
+  for (int sl = 1; sl <= P0.nslots_new; ++sl) { setw(P0.slot_g[sl], r0 + ai); ai += 2; }
+  for (int sl = 0; sl < RB; ++sl) { qz[P0.slot_g[sl]] = r0[ai]; ++ai; }
+  for (int k = 0; k < 5; ++k) { qz[k + 1] = r0[ai]; ++ai; }
+  for (int i = 1; i < np; ++i) {
     const double* r = h + res_off[i];
-    for (int p = passes[i].p_new; p < passes[i].b; ++p) {
-      int q = (i == 0) ? p : passes[i].first_new + (p - L);
-      const double* d = r + (p - passes[i].p_new) * 3;
-      qx[q] = 0.5 * nrm - d[0];
-      qy[q] = 0.5 * nrm - d[1];
-      qz[q] = d[2];
-    }
+    for (int sl = 1; sl <= passes[i].P.nslots_new; ++sl) setw(passes[i].P.slot_g[sl], r + 2 * (sl - 1));
   }
-  (void)stride_of;
+  return QS_OK;
+}
+
+static qs_status expect_small(qs_sim* s, double* qx, double* qy, double* qz) {
+  if (s->N > 12) return QS_EUNSUPPORTED;
+  QS_TRY(ensure_scratch(s, sizeof(double) * (1 + 3 * s->N)));
+  double* d = (double*)s->scratch;
+  if (s->enc == QS_C128) k_expect_small<double2><<<1, TPB, 0, s->stream>>>((const double2*)s->state, s->N, d, nullptr);
+  else if (s->enc == QS_C64) k_expect_small<float2><<<1, TPB, 0, s->stream>>>((const float2*)s->state, s->N, d, nullptr);
+  else k_expect_small<uint16_t><<<1, TPB, 0, s->stream>>>((const uint16_t*)s->state, s->N, d, (const A2Dev*)s->a2dev);
+  QS_LAUNCH_CHECK();
+  QS_TRY(ensure_hbuf(s, sizeof(double) * (1 + 3 * s->N)));
+  QS_CUDA(cudaMemcpyAsync(s->hbuf, d, sizeof(double) * (1 + 3 * s->N), cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(cudaStreamSynchronize(s->stream));
+  const double* h = (const double*)s->hbuf;
+  for (int q = 0; q < s->N; ++q) {
+    qx[q] = 0.5 * h[0] - h[1 + 3 * q];
+    qy[q] = 0.5 * h[0] - h[2 + 3 * q];
+    qz[q] = h[3 + 3 * q];
+  }
   return QS_OK;
 }
 
 qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz) {
-  if (s->enc == QS_C128) return expect_impl<double2>(s, qx, qy, qz);
-  if (s->enc == QS_C64) return expect_impl<float2>(s, qx, qy, qz);
-  return QS_EUNSUPPORTED;
+  if (s->enc == QS_C128 && s->N >= 12) return expect_impl<double, 4, 1>(s, qx, qy, qz);
+  if (s->enc == QS_C64 && s->N >= 13) return expect_impl<float, 5, 0>(s, qx, qy, qz);
+  if (s->enc == QS_ADAPT2 && s->N >= 13) return expect_impl<float, 5, 2>(s, qx, qy, qz);
+  return expect_small(s, qx, qy, qz);
 }
 
 template <typename A>
@@ -411,7 +639,8 @@ static qs_status marginal_impl(qs_sim* s, const int* qubits, int nq, double* out
   const uint64_t nthreads = R << nseg_log;
   QS_TRY(ensure_scratch(s, (size_t)(nthreads + R) * sizeof(double)));
   double* part = (double*)s->scratch;
-  k_marginal<A><<<(unsigned)((nthreads + TPB - 1) / TPB), TPB, 0, s->stream>>>((const A*)s->state, g, part);
+  k_marginal<A><<<(unsigned)((nthreads + TPB - 1) / TPB), TPB, 0, s->stream>>>((const A*)s->state, g, part,
+                                                                             (const A2Dev*)s->a2dev);
   QS_LAUNCH_CHECK();
   double* res = part + nthreads;
   // column sums over the 2^nseg_log segment rows, fixed order
@@ -431,5 +660,11 @@ static qs_status marginal_impl(qs_sim* s, const int* qubits, int nq, double* out
 qs_status launch_marginal(qs_sim* s, const int* qubits, int nq, double* out) {
   if (s->enc == QS_C128) return marginal_impl<double2>(s, qubits, nq, out);
   if (s->enc == QS_C64) return marginal_impl<float2>(s, qubits, nq, out);
-  return QS_EUNSUPPORTED;
+  return marginal_impl<uint16_t>(s, qubits, nq, out);
+}
+
+qs_status sum_partials(qs_sim* s, const double* part, int n, double* out) {
+  k_sum_columns<<<1, TPB, 0, s->stream>>>(part, n, 1, out);
+  QS_LAUNCH_CHECK();
+  return QS_OK;
 }

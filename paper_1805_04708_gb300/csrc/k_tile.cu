@@ -1,15 +1,22 @@
-// Shared-memory tile passes: several gates per read and write of the state
-// (the gate fusion that the end of Sec. 5.2 proposes for raising arithmetic
-// intensity; here every gate keeps its own 2x2 and the fusion is in the data
-// movement).
+// Tile passes: several gates per read and write of the state (the gate
+// fusion that the end of Sec. 5.2 proposes to raise arithmetic intensity;
+// every gate keeps its own 2x2 matrix, the fusion is in the data movement).
 //
-// A tile is the 2^b amplitudes whose index bits outside the tile bit set B
-// are fixed.  B always holds the low L index bits (contiguous runs of 2^L
-// amplitudes, 512 B) plus the targets of the gates in the pass.  A gate may
-// join the pass when its target is in B, or when it is diagonal (its target
-// bit is then fixed per tile and the gate is a per-tile phase); controls may
-// be anywhere (a control outside B is a per-tile condition).  Gate order is
-// kept, so the result equals the per-gate sweep up to rounding order.
+// A tile is the 2^b amplitudes whose index bits outside the tile bit set are
+// fixed; the set holds the low 6 index bits (512-byte runs) plus the targets
+// of the pass's gates.  Inside a CTA of 256 threads the b local bits are
+// split three ways:
+//   local bit 0 and RB-1 more local bits  -> register slots (2^RB amplitudes
+//                                             per thread, updated in registers)
+//   local bits 1..5                         -> the 32 lanes (updated with one
+//                                             warp shuffle per amplitude)
+//   the remaining 3 local bits              -> the 8 warps
+// A gate on a register bit or a lane bit runs without shared memory; a gate on
+// a warp bit first swaps that bit into a register slot by one shared-memory
+// transpose.  Diagonal gates run in place whatever their target (the target
+// bit is known for every element), and controls may be any bit (a control
+// outside the tile is a per-tile condition).  Gate order is kept, so the
+// result equals the per-gate sweep up to rounding order.
 #include "internal.cuh"
 #include "cplx.cuh"
 #include <string.h>
@@ -17,15 +24,37 @@
 
 namespace {
 
-constexpr int TPB = 512;
-constexpr int MAX_OPS = 48;
+constexpr int TPB = 256;      // 8 warps
+constexpr int LANE_BITS = 5;  // local bits 1..5
+constexpr int WARP_BITS = 3;
+constexpr int MAX_TOPS = 96;
 
-struct TileParams {
-  int N, b, L;
+enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5 };
+
+struct TOp {
+  uint8_t type, kind, c0, c1;
+  uint8_t a;           // T_REG / T_DIAG_REG: register slot; T_LANE: lane bit; T_DIAG_THR: local bit
+  uint8_t pad[3];
+  uint32_t smask;      // control bits among the register slots (bits of j)
+  uint32_t tmask;      // control bits among lane / warp local bits (local-index mask)
+  uint64_t gmask;      // control bits outside the tile
+  uint64_t gtbit;      // T_DIAG_OUT: the target bit (global)
+  float uf[8];
+  double ud[8];
+};
+struct TMap {
+  uint8_t reg[8];      // local bit of register slot s (reg[0] = 0)
+  uint8_t warp[4];     // local bit of warp bit k
+};
+
+struct TileParams2 {
+  int N, b;
   uint64_t out_mask;   // global bits outside the tile
-  int hb[16];          // global positions of tile bits L..b-1
+  uint8_t gpos[20];    // global position of local bit k
+  TMap init, fin;      // register / warp assignment at load and at store
   int nops;
-  TileOp ops[MAX_OPS];
+  TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
+  TMap maps[16];
 };
 
 __device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
@@ -37,107 +66,251 @@ __device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
   return r;
 }
 
-template <typename R> __device__ __forceinline__ Cx<R> opc(const TileOp& o, int k) {
-  return cx<R>((R)o.u[2 * k], (R)o.u[2 * k + 1]);
+template <typename R> __device__ __forceinline__ Cx<R> ucx(const TOp& o, int k);
+template <> __device__ __forceinline__ Cx<float> ucx<float>(const TOp& o, int k) { return cx<float>(o.uf[2 * k], o.uf[2 * k + 1]); }
+template <> __device__ __forceinline__ Cx<double> ucx<double>(const TOp& o, int k) { return cx<double>(o.ud[2 * k], o.ud[2 * k + 1]); }
+
+// local index of register j under map m, given the thread part tl
+template <int RB>
+__device__ __forceinline__ uint32_t lidx(const TMap& m, int j, uint32_t tl) {
+  uint32_t l = tl;
+#pragma unroll
+  for (int s = 0; s < RB; ++s)
+    if ((j >> s) & 1) l |= 1u << m.reg[s];
+  return l;
+}
+__device__ __forceinline__ uint32_t thread_part(const TMap& m, int lane, int warp) {
+  uint32_t l = (uint32_t)lane << 1;
+#pragma unroll
+  for (int k = 0; k < WARP_BITS; ++k)
+    if ((warp >> k) & 1) l |= 1u << m.warp[k];
+  return l;
+}
+// global offset (within the tile) of local index bits >= 6
+__device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b) {
+  uint64_t g = l & 63u;
+  for (int k = 6; k < b; ++k)
+    if ((l >> k) & 1) g |= 1ull << gpos[k];
+  return g;
 }
 
-template <typename R, typename F>
-__device__ __forceinline__ void pairs(Cx<R>* t, int b, int p, uint32_t lmask, const F& f) {
-  const int npairs = 1 << (b - 1);
-  for (int j = threadIdx.x; j < npairs; j += TPB) {
-    const uint32_t l0 = (uint32_t)ins0((uint64_t)j, p);
-    if ((l0 & lmask) != lmask) continue;
-    const uint32_t l1 = l0 | (1u << p);
-    Cx<R> a0 = t[l0], a1 = t[l1];
-    f.pair(a0, a1);
-    t[l0] = a0;
-    t[l1] = a1;
+// --- register-slot pair op, slot S fixed at compile time -----------------------------
+template <typename R, int RB, int S, typename F>
+__device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) {
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    if ((j >> S) & 1) continue;
+    if ((j & (int)smask) != (int)smask) continue;
+    f.pair(v[j], v[j | (1 << S)]);
+  }
+}
+template <typename R, int RB, typename F>
+__device__ __forceinline__ void reg_op(Cx<R>* v, int s, uint32_t smask, const F& f) {
+  switch (s) {
+    case 0: reg_pairs<R, RB, 0>(v, smask, f); break;
+    case 1: if (RB > 1) reg_pairs<R, RB, (RB > 1 ? 1 : 0)>(v, smask, f); break;
+    case 2: if (RB > 2) reg_pairs<R, RB, (RB > 2 ? 2 : 0)>(v, smask, f); break;
+    case 3: if (RB > 3) reg_pairs<R, RB, (RB > 3 ? 3 : 0)>(v, smask, f); break;
+    case 4: if (RB > 4) reg_pairs<R, RB, (RB > 4 ? 4 : 0)>(v, smask, f); break;
+    default: if (RB > 5) reg_pairs<R, RB, (RB > 5 ? 5 : 0)>(v, smask, f); break;
   }
 }
 
-template <typename R, typename A>
-__global__ void __launch_bounds__(TPB) k_tile(A* __restrict__ s, const __grid_constant__ TileParams P) {
+template <typename R> __device__ __forceinline__ R uscal(const TOp& o) {
+  if constexpr (sizeof(R) == 4) return o.uf[0]; else return o.ud[0];
+}
+
+template <typename R> __device__ __forceinline__ R shx(R x, int m);
+template <> __device__ __forceinline__ float shx<float>(float x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+template <> __device__ __forceinline__ double shx<double>(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+
+// lane-bit op: partner values by shuffle, each lane keeps its own output
+template <typename R, int RB>
+__device__ __forceinline__ void lane_op(Cx<R>* v, const TOp& o, int lane, bool tok) {
+  const int m = 1 << o.a;
+  const bool hi = (lane >> o.a) & 1;
+  Cx<R> u00 = ucx<R>(o, 0), u01 = ucx<R>(o, 1), u10 = ucx<R>(o, 2), u11 = ucx<R>(o, 3);
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+    if (!tok || (j & (int)o.smask) != (int)o.smask) continue;
+    Cx<R> a0 = hi ? p : v[j], a1 = hi ? v[j] : p;
+    if constexpr (sizeof(R) == 4) {
+      v[j] = hi ? cmac2(u10, a0, u11, a1) : cmac2(u00, a0, u01, a1);
+      continue;
+    }
+    switch (o.kind) {
+      case GK_HAD: {
+        const R s = uscal<R>(o);
+        v[j] = hi ? cx<R>((a0.x - a1.x) * s, (a0.y - a1.y) * s) : cx<R>((a0.x + a1.x) * s, (a0.y + a1.y) * s);
+        break;
+      }
+      case GK_ANTI:
+        v[j] = hi ? cmul_code(a0, u10, o.c1) : cmul_code(a1, u01, o.c0);
+        break;
+      case GK_DIAG:
+        v[j] = hi ? cmul_code(a1, u11, o.c1) : cmul_code(a0, u00, o.c0);
+        break;
+      default:
+        v[j] = hi ? cmac2(u10, a0, u11, a1) : cmac2(u00, a0, u01, a1);
+    }
+  }
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
+                                          int lane) {
+  if constexpr (sizeof(R) == 4) {
+    const float4* s4 = (const float4*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+      float4 x = s4[(base + woff + roff[jj] + ((uint64_t)lane << 1)) >> 1];
+      v[2 * jj] = cx<float>(x.x, x.y);
+      v[2 * jj + 1] = cx<float>(x.z, x.w);
+    }
+  } else {
+    const double2* s2 = (const double2*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+      const uint64_t g = base + woff + roff[jj] + ((uint64_t)lane << 1);
+      double2 x = s2[g], y = s2[g + 1];
+      v[2 * jj] = cx<double>(x.x, x.y);
+      v[2 * jj + 1] = cx<double>(y.x, y.y);
+    }
+  }
+}
+template <typename R, int RB>
+__device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
+                                           int lane) {
+  if constexpr (sizeof(R) == 4) {
+    float4* s4 = (float4*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj)
+      s4[(base + woff + roff[jj] + ((uint64_t)lane << 1)) >> 1] =
+          make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+  } else {
+    double2* s2 = (double2*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+      const uint64_t g = base + woff + roff[jj] + ((uint64_t)lane << 1);
+      s2[g] = make_double2(v[2 * jj].x, v[2 * jj].y);
+      s2[g + 1] = make_double2(v[2 * jj + 1].x, v[2 * jj + 1].y);
+    }
+  }
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __grid_constant__ TileParams2 P) {
   extern __shared__ unsigned char smraw[];
-  Cx<R>* t = (Cx<R>*)smraw;
-  uint64_t* off = (uint64_t*)(smraw + (sizeof(Cx<R>) << P.b));
-  const int nh = 1 << (P.b - P.L);
-  for (int h = threadIdx.x; h < nh; h += TPB) {
-    uint64_t o = 0;
-    for (int k = 0; k < P.b - P.L; ++k) o |= (uint64_t)((h >> k) & 1) << P.hb[k];
-    off[h] = o;
+  constexpr int NR = 1 << RB;
+  // global offsets of the register part (pairs jj: slots 1..RB-1) at load / store
+  uint64_t* roff_in = (uint64_t*)smraw;
+  uint64_t* roff_out = roff_in + NR / 2;
+  Cx<R>* xb = (Cx<R>*)(smraw + NR * sizeof(uint64_t));  // transpose buffer, 2^b elements
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < NR / 2) {
+    roff_in[threadIdx.x] = goff(lidx<RB>(P.init, 2 * threadIdx.x, 0), P.gpos, P.b);
+    roff_out[threadIdx.x] = goff(lidx<RB>(P.fin, 2 * threadIdx.x, 0), P.gpos, P.b);
   }
-  const int tsize = 1 << P.b;
-  const int lm = (1 << P.L) - 1;
-  const uint64_t ntiles = 1ull << (P.N - P.b);
   __syncthreads();
+  const uint64_t woff_in = goff(thread_part(P.init, 0, warp), P.gpos, P.b);
+  const uint64_t woff_out = goff(thread_part(P.fin, 0, warp), P.gpos, P.b);
+  const uint64_t ntiles = 1ull << (P.N - P.b);
+  Cx<R> v[NR];
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
     const uint64_t base = deposit_t(tau, P.out_mask);
-    // load (2 amplitudes per 16-byte access for complex64, 1 for complex128)
-    if (sizeof(R) == 4) {
-      const float4* s4 = (const float4*)s;
-      float4* t4 = (float4*)t;
-#pragma unroll 4
-      for (int v = threadIdx.x; v < tsize / 2; v += TPB) {
-        const int l = 2 * v;
-        t4[v] = s4[(base + off[l >> P.L] + (l & lm)) >> 1];
-      }
-    } else {
-      const double2* s2 = (const double2*)s;
-      double2* t2 = (double2*)t;
-#pragma unroll 4
-      for (int l = threadIdx.x; l < tsize; l += TPB) t2[l] = s2[base + off[l >> P.L] + (l & lm)];
-    }
-    __syncthreads();
+    load_tile<R, RB>(s, v, base, roff_in, woff_in, lane);
+    TMap cur = P.init;
+    uint32_t tl = thread_part(cur, lane, warp);
+    int mapi = 0;
     for (int i = 0; i < P.nops; ++i) {
-      const TileOp& o = P.ops[i];
-      if ((base & o.gmask) != o.gmask) continue;  // an outer control is 0 for this tile
-      if (o.p < 0) {
-        // diagonal gate on a qubit outside the tile: one factor per tile
-        const bool one = (base & o.gtbit) != 0;
-        const int code = one ? o.c1 : o.c0;
-        if (code == 0) continue;
-        OpMul<R> m;
-        m.f = opc<R>(o, one ? 3 : 0);
-        m.c = code;
-        for (int l = threadIdx.x; l < tsize; l += TPB)
-          if (((uint32_t)l & o.lmask) == o.lmask) m.one(t[l]);
-      } else {
-        switch (o.kind) {
-          case GK_HAD: { OpHad<R> f; f.s = (R)o.u[0]; pairs<R>(t, P.b, o.p, o.lmask, f); break; }
-          case GK_DIAG: {
-            OpDiag<R> f; f.d0 = opc<R>(o, 0); f.d1 = opc<R>(o, 3); f.c0 = o.c0; f.c1 = o.c1;
-            pairs<R>(t, P.b, o.p, o.lmask, f);
-            break;
-          }
-          case GK_ANTI: {
-            OpAnti<R> f; f.f01 = opc<R>(o, 1); f.f10 = opc<R>(o, 2); f.c0 = o.c0; f.c1 = o.c1;
-            pairs<R>(t, P.b, o.p, o.lmask, f);
-            break;
-          }
-          default: {
-            OpDense<R> f; f.u00 = opc<R>(o, 0); f.u01 = opc<R>(o, 1); f.u10 = opc<R>(o, 2); f.u11 = opc<R>(o, 3);
-            pairs<R>(t, P.b, o.p, o.lmask, f);
+      const TOp& o = P.ops[i];
+      if (o.type == T_XPOSE) {
+        // write every register at its local index, read back under the new map
+#pragma unroll
+        for (int jj = 0; jj < NR / 2; ++jj) {
+          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
+          if constexpr (sizeof(R) == 4) {
+            ((float4*)xb)[l >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+          } else {
+            xb[l] = v[2 * jj];
+            xb[l + 1] = v[2 * jj + 1];
           }
         }
+        __syncthreads();
+        cur = P.maps[mapi++];
+        tl = thread_part(cur, lane, warp);
+#pragma unroll
+        for (int jj = 0; jj < NR / 2; ++jj) {
+          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
+          if constexpr (sizeof(R) == 4) {
+            float4 x = ((const float4*)xb)[l >> 1];
+            v[2 * jj] = cx<float>(x.x, x.y);
+            v[2 * jj + 1] = cx<float>(x.z, x.w);
+          } else {
+            v[2 * jj] = xb[l];
+            v[2 * jj + 1] = xb[l + 1];
+          }
+        }
+        __syncthreads();
+        continue;
       }
-      __syncthreads();
-    }
-    // store
-    if (sizeof(R) == 4) {
-      float4* s4 = (float4*)s;
-      const float4* t4 = (const float4*)t;
-#pragma unroll 4
-      for (int v = threadIdx.x; v < tsize / 2; v += TPB) {
-        const int l = 2 * v;
-        s4[(base + off[l >> P.L] + (l & lm)) >> 1] = t4[v];
+      if ((base & o.gmask) != o.gmask) continue;          // an outer control is 0
+      const bool tok = (tl & o.tmask) == o.tmask;         // lane / warp controls
+      switch (o.type) {
+        case T_REG: {
+          if (!tok) break;
+          if constexpr (sizeof(R) == 4) {
+            // complex64: every non-diagonal gate as a dense 2x2 (exact for the
+            // unit entries of X / Y / CNOT / TOFFOLI); one code path keeps the
+            // kernel small
+            OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
+            reg_op<R, RB>(v, o.a, o.smask, f);
+          } else {
+            // complex128: the FP64 pipe is the bound, so keep the cheaper forms
+            switch (o.kind) {
+              case GK_HAD: { OpHad<R> f; f.s = uscal<R>(o); reg_op<R, RB>(v, o.a, o.smask, f); break; }
+              case GK_ANTI: { OpAnti<R> f; f.f01 = ucx<R>(o, 1); f.f10 = ucx<R>(o, 2); f.c0 = o.c0; f.c1 = o.c1; reg_op<R, RB>(v, o.a, o.smask, f); break; }
+              default: {
+                OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
+                reg_op<R, RB>(v, o.a, o.smask, f);
+              }
+            }
+          }
+          break;
+        }
+        case T_LANE:
+          lane_op<R, RB>(v, o, lane, tok);
+          break;
+        case T_DIAG_REG:
+        case T_DIAG_THR:
+        case T_DIAG_OUT: {
+          if (!tok) break;
+          const Cx<R> d0 = ucx<R>(o, 0), d1 = ucx<R>(o, 3);
+          if (o.type == T_DIAG_REG) {
+            const int sl = o.a;
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+              if ((j & (int)o.smask) != (int)o.smask) continue;
+              const bool one = (j >> sl) & 1;
+              if constexpr (sizeof(R) == 4) v[j] = cmul_code(v[j], one ? d1 : d0, 4);
+              else v[j] = one ? cmul_code(v[j], d1, o.c1) : cmul_code(v[j], d0, o.c0);
+            }
+          } else {
+            const bool one = (o.type == T_DIAG_THR) ? ((tl >> o.a) & 1) : ((base & o.gtbit) != 0);
+            const int code = one ? o.c1 : o.c0;
+            if (code == 0) break;
+            const Cx<R> d = one ? d1 : d0;
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+              if ((j & (int)o.smask) == (int)o.smask) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
+          }
+          break;
+        }
+        default: break;
       }
-    } else {
-      double2* s2 = (double2*)s;
-      const double2* t2 = (const double2*)t;
-#pragma unroll 4
-      for (int l = threadIdx.x; l < tsize; l += TPB) s2[base + off[l >> P.L] + (l & lm)] = t2[l];
     }
-    __syncthreads();
+    store_tile<R, RB>(s, v, base, roff_out, woff_out, lane);
   }
 }
 
@@ -146,97 +319,200 @@ __global__ void __launch_bounds__(TPB) k_tile(A* __restrict__ s, const __grid_co
 // ---------------------------------------------------------------------------------
 // planner
 // ---------------------------------------------------------------------------------
-static void close_pass(const qs_gate* gates, const int* gidx, int ng, int N, int b, uint64_t S,
-                       TilePass* tp, TileOp* ops, int* nops_total) {
-  // pad S to b bits with the lowest unused bits
-  for (int q = 0; q < N && __builtin_popcountll(S) < b; ++q) S |= 1ull << q;
-  tp->b = __builtin_popcountll(S);
-  int k = 0;
+struct PassPlan {
+  TileParams2 P;
+};
+
+static void fill_u(TOp& o, const double* u) {
+  for (int k = 0; k < 8; ++k) { o.ud[k] = u[k]; o.uf[k] = (float)u[k]; }
+}
+
+// Build the op list of one pass.  tile: bitmask of the tile's global bits
+// (contains bits 0..5), gidx: the gates in order.  Returns false if the op
+// list overflows (caller splits the pass).
+static bool build_pass(const qs_gate* gates, const int* gidx, int ng, int N, int b, int RB, uint64_t tile,
+                       TileParams2* P) {
+  memset(P, 0, sizeof *P);
+  P->N = N;
+  P->b = b;
   int local[64];
+  int k = 0;
   for (int q = 0; q < N; ++q) {
     local[q] = -1;
-    if ((S >> q) & 1) { tp->bits[k] = q; local[q] = k; ++k; }
+    if ((tile >> q) & 1) { P->gpos[k] = (uint8_t)q; local[q] = k; ++k; }
   }
-  tp->op_begin = *nops_total;
-  tp->nops = 0;
+  const uint64_t all = (N >= 64) ? ~0ull : ((1ull << N) - 1);
+  P->out_mask = all & ~tile;
+  // high local bits 6..b-1: RB-1 register slots + WARP_BITS warp bits
+  const int nhigh = b - 6;
+  // next use of each high local bit as a non-diagonal target, for eviction
+  // choices; initial registers = the first RB-1 distinct high targets
+  int slot_of[32];
+  for (int i = 0; i < 32; ++i) slot_of[i] = -1;
+  TMap cur;
+  memset(&cur, 0, sizeof cur);
+  cur.reg[0] = 0;
+  int nreg = 1;
+  for (int i = 0; i < ng && nreg < RB; ++i) {
+    const qs_gate& g = gates[gidx[i]];
+    if (classify_u2(g.u).kind == GK_DIAG) continue;
+    int p = local[g.target];
+    if (p >= 6 && slot_of[p] < 0) { slot_of[p] = nreg; cur.reg[nreg++] = (uint8_t)p; }
+  }
+  for (int p = 6; p < b && nreg < RB; ++p)
+    if (slot_of[p] < 0) { slot_of[p] = nreg; cur.reg[nreg++] = (uint8_t)p; }
+  int nw = 0;
+  for (int p = 6; p < b; ++p)
+    if (slot_of[p] < 0) cur.warp[nw++] = (uint8_t)p;
+  (void)nhigh;
+  P->init = cur;
+  int nops = 0, nmaps = 0;
+  auto reg_slot = [&](int p) -> int {
+    if (p == 0) return 0;
+    for (int s = 1; s < RB; ++s) if (cur.reg[s] == p) return s;
+    return -1;
+  };
   for (int i = 0; i < ng; ++i) {
     const qs_gate& g = gates[gidx[i]];
     GateClass gc = classify_u2(g.u);
-    TileOp o;
+    int p = local[g.target];
+    const bool diag = (gc.kind == GK_DIAG);
+    if (!diag && p >= 6 && reg_slot(p) < 0) {
+      // transpose: bring p into the register slot whose next use is farthest
+      if (nops >= MAX_TOPS || nmaps >= 16) return false;
+      int best = 1, bestd = -1;
+      for (int s = 1; s < RB; ++s) {
+        int d = ng + 1;
+        for (int j = i; j < ng; ++j) {
+          const qs_gate& h = gates[gidx[j]];
+          if (classify_u2(h.u).kind != GK_DIAG && local[h.target] == cur.reg[s]) { d = j; break; }
+        }
+        if (d > bestd) { bestd = d; best = s; }
+      }
+      int evicted = cur.reg[best];
+      cur.reg[best] = (uint8_t)p;
+      for (int w = 0; w < WARP_BITS; ++w)
+        if (cur.warp[w] == p) cur.warp[w] = (uint8_t)evicted;
+      TOp x;
+      memset(&x, 0, sizeof x);
+      x.type = T_XPOSE;
+      P->ops[nops++] = x;
+      P->maps[nmaps++] = cur;
+    }
+    if (nops >= MAX_TOPS) return false;
+    TOp o;
     memset(&o, 0, sizeof o);
-    o.kind = gc.kind;
-    o.c0 = gc.c0;
-    o.c1 = gc.c1;
-    o.p = local[g.target];
-    o.gtbit = (o.p < 0) ? (1ull << g.target) : 0;
+    o.kind = (uint8_t)gc.kind;
+    o.c0 = (uint8_t)gc.c0;
+    o.c1 = (uint8_t)gc.c1;
+    fill_u(o, g.u);
     for (int c = 0; c < g.nc; ++c) {
       int q = g.controls[c];
-      if (local[q] >= 0) o.lmask |= 1u << local[q];
-      else o.gmask |= 1ull << q;
+      int lq = local[q];
+      if (lq < 0) { o.gmask |= 1ull << q; continue; }
+      int s = reg_slot(lq);
+      if (s >= 0) o.smask |= 1u << s;
+      else o.tmask |= 1u << lq;
     }
-    memcpy(o.u, g.u, sizeof o.u);
-    ops[*nops_total + tp->nops] = o;
-    tp->nops++;
+    if (p < 0) {
+      o.type = T_DIAG_OUT;
+      o.gtbit = 1ull << g.target;
+    } else if (diag) {
+      int s = reg_slot(p);
+      if (s >= 0) { o.type = T_DIAG_REG; o.a = (uint8_t)s; }
+      else { o.type = T_DIAG_THR; o.a = (uint8_t)p; }
+    } else if (p >= 1 && p <= 5) {
+      o.type = T_LANE;
+      o.a = (uint8_t)(p - 1);
+    } else {
+      o.type = T_REG;
+      o.a = (uint8_t)reg_slot(p);
+    }
+    P->ops[nops++] = o;
   }
-  *nops_total += tp->nops;
+  P->nops = nops;
+  P->fin = cur;
+  return true;
 }
 
-int plan_tile_passes(const qs_gate* gates, int n, int N, int b, int L, TilePass* passes, int max_passes,
-                     TileOp* ops, int max_ops) {
-  (void)max_ops;
-  int np = 0, nops = 0;
-  const uint64_t lowS = (L >= 64) ? ~0ull : ((1ull << L) - 1);
-  uint64_t S = lowS;
+int tile_register_bits(qs_encoding enc) { return enc == QS_C128 ? 4 : 5; }
+int tile_bits(qs_encoding enc) { return tile_register_bits(enc) + LANE_BITS + WARP_BITS; }
+
+// Greedy: extend the current pass while the union of the non-diagonal
+// targets fits in the tile; a pass whose op list overflows is split.
+static qs_status run_pass(qs_sim* s, const qs_gate* gates, const int* gidx, int ng, uint64_t tile, int* launched,
+                          PassTimer* timer);
+
+qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer) {
+  const int b = tile_bits(s->enc);
+  const int N = s->N;
   int* gidx = (int*)malloc(sizeof(int) * (size_t)(n + 1));
-  int ng = 0;
-  for (int i = 0; i < n; ++i) {
+  if (!gidx) return QS_ENOMEM;
+  const uint64_t low = 63ull;
+  uint64_t S = low;
+  int ng = 0, launched = 0;
+  qs_status st = QS_OK;
+  auto flush = [&](uint64_t tile) -> qs_status {
+    // pad the tile to b bits with the lowest unused bits
+    for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
+    return run_pass(s, gates, gidx, ng, tile, &launched, timer);
+  };
+  for (int i = 0; i < n && st == QS_OK; ++i) {
     GateClass gc = classify_u2(gates[i].u);
     if (gc.kind == GK_IDENT) continue;
     uint64_t need = (gc.kind == GK_DIAG) ? 0ull : (1ull << gates[i].target);
     uint64_t S2 = S | need;
-    if ((__builtin_popcountll(S2) > b || ng >= MAX_OPS) && ng > 0) {
-      if (np < max_passes) close_pass(gates, gidx, ng, N, b, S, &passes[np++], ops, &nops);
+    if ((__builtin_popcountll(S2) > b || ng >= MAX_TOPS / 2) && ng > 0) {
+      st = flush(S);
       ng = 0;
-      S = lowS | need;
+      S = low | need;
     } else {
       S = S2;
     }
     gidx[ng++] = i;
   }
-  if (ng > 0 && np < max_passes) close_pass(gates, gidx, ng, N, b, S, &passes[np++], ops, &nops);
+  if (st == QS_OK && ng > 0) st = flush(S);
   free(gidx);
-  return np;
+  if (n_passes) *n_passes = launched;
+  return st;
 }
 
-qs_status launch_tile_pass(qs_sim* s, const TilePass& pass, const TileOp* ops) {
-  TileParams P;
-  memset(&P, 0, sizeof P);
-  P.N = s->N;
-  P.b = pass.b;
-  // low contiguous bits of the tile
-  int L = 0;
-  while (L < pass.b && pass.bits[L] == L) ++L;
-  P.L = L;
-  uint64_t tmask = 0;
-  for (int k = 0; k < pass.b; ++k) tmask |= 1ull << pass.bits[k];
-  for (int k = L; k < pass.b; ++k) P.hb[k - L] = pass.bits[k];
-  const uint64_t all = (s->N >= 64) ? ~0ull : ((1ull << s->N) - 1);
-  P.out_mask = all & ~tmask;
-  P.nops = pass.nops;
-  for (int i = 0; i < pass.nops; ++i) P.ops[i] = ops[i];
-  const uint64_t ntiles = 1ull << (s->N - pass.b);
+static qs_status launch_pass(qs_sim* s, const TileParams2& P, PassTimer* timer) {
+  const bool timed = timer && timer->n < timer->max_ev;
+  if (timed) QS_CUDA(cudaEventRecord(timer->ev[2 * timer->n], s->stream));
+  const uint64_t ntiles = 1ull << (s->N - P.b);
+  const uint64_t gmax = (uint64_t)s->num_sms * 4;
+  const unsigned grid = (unsigned)(ntiles < gmax ? ntiles : gmax);
   if (s->enc == QS_C128) {
-    const size_t smem = ((size_t)16 << pass.b) + ((size_t)8 << (pass.b - L));
-    QS_CUDA(cudaFuncSetAttribute(k_tile<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const uint64_t g = (uint64_t)s->num_sms * 3;
-    k_tile<double, double2><<<(unsigned)(ntiles < g ? ntiles : g), TPB, smem, s->stream>>>((double2*)s->state, P);
+    const size_t smem = ((size_t)16 << P.b) + 16 * sizeof(uint64_t);
+    QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tile2<double, 4><<<grid, TPB, smem, s->stream>>>(s->state, P);
   } else {
-    if (L < 1) { qs_set_error("tile pass: complex64 tiles need bit 0"); return QS_EINVAL; }
-    const size_t smem = ((size_t)8 << pass.b) + ((size_t)8 << (pass.b - L));
-    QS_CUDA(cudaFuncSetAttribute(k_tile<float, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const uint64_t g = (uint64_t)s->num_sms * 3;
-    k_tile<float, float2><<<(unsigned)(ntiles < g ? ntiles : g), TPB, smem, s->stream>>>((float2*)s->state, P);
+    const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
+    QS_CUDA(cudaFuncSetAttribute(k_tile2<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tile2<float, 5><<<grid, TPB, smem, s->stream>>>(s->state, P);
   }
   QS_LAUNCH_CHECK();
+  if (timed) {
+    QS_CUDA(cudaEventRecord(timer->ev[2 * timer->n + 1], s->stream));
+    timer->n++;
+  } else if (timer) {
+    timer->n++;
+  }
   return QS_OK;
+}
+
+static qs_status run_pass(qs_sim* s, const qs_gate* gates, const int* gidx, int ng, uint64_t tile, int* launched,
+                          PassTimer* timer) {
+  static thread_local TileParams2 P;
+  const int b = tile_bits(s->enc);
+  if (build_pass(gates, gidx, ng, s->N, b, tile_register_bits(s->enc), tile, &P)) {
+    QS_TRY(launch_pass(s, P, timer));
+    ++*launched;
+    return QS_OK;
+  }
+  // too many ops for one launch: split the gate run in halves (same tile)
+  const int h = ng / 2;
+  QS_TRY(run_pass(s, gates, gidx, h, tile, launched, timer));
+  return run_pass(s, gates, gidx + h, ng - h, tile, launched, timer);
 }

@@ -109,7 +109,7 @@ def test_layered_circuit_n20(q, enc):
 
 
 @pytest.mark.parametrize("enc", ["c128", "c64"])
-@pytest.mark.parametrize("N", [2, 4, 9, 13, 17])
+@pytest.mark.parametrize("N", [2, 4, 9, 12, 13, 14, 17, 22])
 def test_reductions(q, enc, N):
     v0 = rand_state(N, 5 * N) * 0.97
     with q.Sim(N, enc) as s:
@@ -118,9 +118,12 @@ def test_reductions(q, enc, N):
         assert abs(s.norm() - sv.norm(v)) <= 1e-13
         qx, qy, qz = s.expect_xyz()
         rx, ry, rz = sv.expect_xyz(v, N)
-        assert np.max(np.abs(qx - rx)) <= 1e-13
-        assert np.max(np.abs(qy - ry)) <= 1e-13
-        assert np.max(np.abs(qz - rz)) <= 1e-13
+        # complex64 BEGIN MEASUREMENT: FP32 products and <= 32-term FP32 leaf
+        # sums folded into float-float / FP64 accumulators; complex128: FP64
+        tol = 1e-8 if (enc == "c64" and N >= 13) else 1e-13
+        assert np.max(np.abs(qx - rx)) <= tol
+        assert np.max(np.abs(qy - ry)) <= tol
+        assert np.max(np.abs(qz - rz)) <= tol
         g = np.random.default_rng(N)
         for nq in sorted({1, min(3, N), min(N, 7)}):
             qs = [int(x) for x in g.choice(N, nq, replace=False)]
