@@ -28,6 +28,7 @@ constexpr int TPB = 256;      // 8 warps
 constexpr int LANE_BITS = 5;  // local bits 1..5
 constexpr int WARP_BITS = 3;
 constexpr int MAX_TOPS = 96;
+constexpr int LOW_BITS = 4;   // index bits always in the tile (16-amplitude runs)
 
 enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5 };
 
@@ -86,10 +87,11 @@ __device__ __forceinline__ uint32_t thread_part(const TMap& m, int lane, int war
     if ((warp >> k) & 1) l |= 1u << m.warp[k];
   return l;
 }
-// global offset (within the tile) of local index bits >= 6
+// global offset (within the tile) of a local index: local bits 0..3 are
+// index bits 0..3, the others map through gpos
 __device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b) {
-  uint64_t g = l & 63u;
-  for (int k = 6; k < b; ++k)
+  uint64_t g = l & 15u;
+  for (int k = 4; k < b; ++k)
     if ((l >> k) & 1) g |= 1ull << gpos[k];
   return g;
 }
@@ -97,11 +99,40 @@ __device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b)
 // --- register-slot pair op, slot S fixed at compile time -----------------------------
 template <typename R, int RB, int S, typename F>
 __device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) {
+  if (smask == 0) {   // the common case: no control among the register slots
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j)
+      if (!((j >> S) & 1)) f.pair(v[j], v[j | (1 << S)]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+      if ((j >> S) & 1) continue;
+      if ((j & (int)smask) != (int)smask) continue;
+      f.pair(v[j], v[j | (1 << S)]);
+    }
+  }
+}
+
+// diagonal on register slot S: factor d1 where bit S is 1, d0 where it is 0;
+// skip0 / skip1 leave the elements with a unit factor untouched
+template <typename R, int RB, int S>
+__device__ __forceinline__ void reg_diag(Cx<R>* v, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
 #pragma unroll
   for (int j = 0; j < (1 << RB); ++j) {
-    if ((j >> S) & 1) continue;
     if ((j & (int)smask) != (int)smask) continue;
-    f.pair(v[j], v[j | (1 << S)]);
+    const bool one = (j >> S) & 1;
+    if (one ? skip1 : skip0) continue;
+    v[j] = cmul_code(v[j], one ? d1 : d0, 4);
+  }
+}
+template <typename R, int RB>
+__device__ __forceinline__ void reg_diag_rt(Cx<R>* v, int s, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
+  switch (s) {
+    case 0: reg_diag<R, RB, 0>(v, smask, d0, d1, skip0, skip1); break;
+    case 1: reg_diag<R, RB, (RB > 1 ? 1 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+    case 2: reg_diag<R, RB, (RB > 2 ? 2 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+    case 3: reg_diag<R, RB, (RB > 3 ? 3 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+    default: reg_diag<R, RB, (RB > 4 ? 4 : 0)>(v, smask, d0, d1, skip0, skip1); break;
   }
 }
 template <typename R, int RB, typename F>
@@ -130,15 +161,29 @@ __device__ __forceinline__ void lane_op(Cx<R>* v, const TOp& o, int lane, bool t
   const int m = 1 << o.a;
   const bool hi = (lane >> o.a) & 1;
   Cx<R> u00 = ucx<R>(o, 0), u01 = ucx<R>(o, 1), u10 = ucx<R>(o, 2), u11 = ucx<R>(o, 3);
+  if constexpr (sizeof(R) == 4) {
+    // each lane keeps cs * own + cp * partner, with per-lane coefficients
+    const Cx<R> cs = hi ? u11 : u00, cp = hi ? u10 : u01;
+    if (o.smask == 0) {
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (tok) v[j] = cmac2(cs, v[j], cp, p);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (tok && (j & (int)o.smask) == (int)o.smask) v[j] = cmac2(cs, v[j], cp, p);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < (1 << RB); ++j) {
     Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
     if (!tok || (j & (int)o.smask) != (int)o.smask) continue;
     Cx<R> a0 = hi ? p : v[j], a1 = hi ? v[j] : p;
-    if constexpr (sizeof(R) == 4) {
-      v[j] = hi ? cmac2(u10, a0, u11, a1) : cmac2(u00, a0, u01, a1);
-      continue;
-    }
     switch (o.kind) {
       case GK_HAD: {
         const R s = uscal<R>(o);
@@ -164,7 +209,7 @@ __device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base
     const float4* s4 = (const float4*)s;
 #pragma unroll
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-      float4 x = s4[(base + woff + roff[jj] + ((uint64_t)lane << 1)) >> 1];
+      float4 x = s4[(base + woff + roff[jj]) >> 1];
       v[2 * jj] = cx<float>(x.x, x.y);
       v[2 * jj + 1] = cx<float>(x.z, x.w);
     }
@@ -172,7 +217,7 @@ __device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base
     const double2* s2 = (const double2*)s;
 #pragma unroll
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-      const uint64_t g = base + woff + roff[jj] + ((uint64_t)lane << 1);
+      const uint64_t g = base + woff + roff[jj];
       double2 x = s2[g], y = s2[g + 1];
       v[2 * jj] = cx<double>(x.x, x.y);
       v[2 * jj + 1] = cx<double>(y.x, y.y);
@@ -186,13 +231,12 @@ __device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t bas
     float4* s4 = (float4*)s;
 #pragma unroll
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj)
-      s4[(base + woff + roff[jj] + ((uint64_t)lane << 1)) >> 1] =
-          make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+      s4[(base + woff + roff[jj]) >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
   } else {
     double2* s2 = (double2*)s;
 #pragma unroll
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-      const uint64_t g = base + woff + roff[jj] + ((uint64_t)lane << 1);
+      const uint64_t g = base + woff + roff[jj];
       s2[g] = make_double2(v[2 * jj].x, v[2 * jj].y);
       s2[g + 1] = make_double2(v[2 * jj + 1].x, v[2 * jj + 1].y);
     }
@@ -213,8 +257,8 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
     roff_out[threadIdx.x] = goff(lidx<RB>(P.fin, 2 * threadIdx.x, 0), P.gpos, P.b);
   }
   __syncthreads();
-  const uint64_t woff_in = goff(thread_part(P.init, 0, warp), P.gpos, P.b);
-  const uint64_t woff_out = goff(thread_part(P.fin, 0, warp), P.gpos, P.b);
+  const uint64_t woff_in = goff(thread_part(P.init, lane, warp), P.gpos, P.b);
+  const uint64_t woff_out = goff(thread_part(P.fin, lane, warp), P.gpos, P.b);
   const uint64_t ntiles = 1ull << (P.N - P.b);
   Cx<R> v[NR];
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
@@ -288,13 +332,16 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
           if (!tok) break;
           const Cx<R> d0 = ucx<R>(o, 0), d1 = ucx<R>(o, 3);
           if (o.type == T_DIAG_REG) {
-            const int sl = o.a;
+            if constexpr (sizeof(R) == 4) {
+              reg_diag_rt<R, RB>(v, o.a, o.smask, d0, d1, o.c0 == 0, o.c1 == 0);
+            } else {
+              const int sl = o.a;
 #pragma unroll
-            for (int j = 0; j < NR; ++j) {
-              if ((j & (int)o.smask) != (int)o.smask) continue;
-              const bool one = (j >> sl) & 1;
-              if constexpr (sizeof(R) == 4) v[j] = cmul_code(v[j], one ? d1 : d0, 4);
-              else v[j] = one ? cmul_code(v[j], d1, o.c1) : cmul_code(v[j], d0, o.c0);
+              for (int j = 0; j < NR; ++j) {
+                if ((j & (int)o.smask) != (int)o.smask) continue;
+                const bool one = (j >> sl) & 1;
+                v[j] = one ? cmul_code(v[j], d1, o.c1) : cmul_code(v[j], d0, o.c0);
+              }
             }
           } else {
             const bool one = (o.type == T_DIAG_THR) ? ((tl >> o.a) & 1) : ((base & o.gtbit) != 0);
@@ -335,12 +382,27 @@ static bool build_pass(const qs_gate* gates, const int* gidx, int ng, int N, int
   memset(P, 0, sizeof *P);
   P->N = N;
   P->b = b;
+  // local bits: 0..3 = index bits 0..3 (runs of 16 amplitudes), 4..5 = the
+  // two high tile qubits with the fewest non-diagonal gates in the pass
+  // (lane qubits, updated by shuffles), 6..b-1 = the other tile qubits
   int local[64];
-  int k = 0;
-  for (int q = 0; q < N; ++q) {
-    local[q] = -1;
-    if ((tile >> q) & 1) { P->gpos[k] = (uint8_t)q; local[q] = k; ++k; }
+  int uses[64];
+  for (int q = 0; q < 64; ++q) { local[q] = -1; uses[q] = 0; }
+  for (int i = 0; i < ng; ++i) {
+    const qs_gate& g = gates[gidx[i]];
+    if (classify_u2(g.u).kind != GK_DIAG) uses[g.target]++;
   }
+  for (int q = 0; q < LOW_BITS; ++q) { P->gpos[q] = (uint8_t)q; local[q] = q; }
+  int k = LOW_BITS;
+  for (int pick = 0; pick < 2; ++pick) {
+    int best = -1;
+    for (int q = LOW_BITS; q < N; ++q)
+      if (((tile >> q) & 1) && local[q] < 0 && (best < 0 || uses[q] < uses[best])) best = q;
+    P->gpos[k] = (uint8_t)best;
+    local[best] = k++;
+  }
+  for (int q = LOW_BITS; q < N; ++q)
+    if (((tile >> q) & 1) && local[q] < 0) { P->gpos[k] = (uint8_t)q; local[q] = k++; }
   const uint64_t all = (N >= 64) ? ~0ull : ((1ull << N) - 1);
   P->out_mask = all & ~tile;
   // high local bits 6..b-1: RB-1 register slots + WARP_BITS warp bits
@@ -448,7 +510,7 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
   const int N = s->N;
   int* gidx = (int*)malloc(sizeof(int) * (size_t)(n + 1));
   if (!gidx) return QS_ENOMEM;
-  const uint64_t low = 63ull;
+  const uint64_t low = (1ull << LOW_BITS) - 1;
   uint64_t S = low;
   int ng = 0, launched = 0;
   qs_status st = QS_OK;
