@@ -197,6 +197,24 @@ qs_status expect_xyz(qs_sim* sim, double* qx, double* qy, double* qz);
  * |a|^2, for k = 0..2^nq - 1 (1 <= nq <= 24).  out: host, 2^nq doubles. */
 qs_status measure_probs(qs_sim* sim, const int* qubits, int nq, double* out);
 
+/* As measure_probs, for a caller that cannot allocate device memory (its
+ * memory is owned by another framework's pool, or it runs in a loop that must
+ * not enter the driver's allocator).  The paper has no counterpart: this is a
+ * calling convention of this library, not a step of the method.
+ * state: device, the caller's 2^N amplitudes (QS_C128 or QS_C64 layout; other
+ * encodings give QS_EUNSUPPORTED); qubits, out: host, as in measure_probs;
+ * cuda_stream: the stream the work is ordered on (NULL = default stream).
+ * Allocates nothing: the scratch is a fixed array of 2^18 + 2^16 doubles
+ * (2.5 MiB) in the library's device memory, held by every GPU that loads the
+ * library until the process exits, so nq is limited to 16 (larger gives
+ * QS_EINVAL).  The first call on a device looks the array's address up on
+ * that device; make it before any stream capture.  Every call shares the one
+ * array, which keeps the last call's contents (each call writes every entry
+ * it reads): calls that overlap on the GPU, on any streams, race and give
+ * wrong results.  Synchronises cuda_stream before returning. */
+qs_status measure_probs_static(const void* state, int N, qs_encoding enc, const int* qubits, int nq,
+                               double* out, void* cuda_stream);
+
 /* ---- raw state access (parity dumps) ------------------------------------- */
 /* Copy the raw amplitudes (2^N * bytes-per-amplitude bytes, layout as in
  * qs_encoding) to / from host memory.  For QS_ADAPT2, r0r1 (host, 2 doubles,

@@ -668,3 +668,107 @@ qs_status sum_partials(qs_sim* s, const double* part, int n, double* out) {
   QS_LAUNCH_CHECK();
   return QS_OK;
 }
+
+// =====================================================================================
+// measure_probs_static: the register marginal without any allocation.
+//
+// Some callers cannot allocate device memory: a host framework whose memory
+// pool already owns the device's memory, or a latency-critical loop that must
+// not enter the driver's allocator.  This entry point works on a device buffer
+// the caller already holds and keeps its scratch in a fixed array in the
+// library's device memory (QS_STATIC_SCRATCH_DOUBLES doubles, 2.5 MiB, held by
+// every GPU that loads the library until the process exits).
+// =====================================================================================
+#include <mutex>
+
+#define QS_STATIC_MAX_NQ 16
+#define QS_STATIC_PARTIALS (1 << 18)
+#define QS_STATIC_SCRATCH_DOUBLES (QS_STATIC_PARTIALS + (1 << QS_STATIC_MAX_NQ))
+#define QS_STATIC_MAX_DEVICES 64
+
+static __device__ __align__(256) double g_static_scratch[QS_STATIC_SCRATCH_DOUBLES];
+
+static std::mutex g_static_mu;
+static double* g_static_addr[QS_STATIC_MAX_DEVICES];
+
+// Device address of g_static_scratch on the current device.  The name of the
+// array in host code is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+static qs_status static_scratch_addr(double** out) {
+  int dev = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= QS_STATIC_MAX_DEVICES) {
+    qs_set_error("measure_probs_static: device %d beyond the %d supported", dev, QS_STATIC_MAX_DEVICES);
+    return QS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      qs_set_error("measure_probs_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return QS_ECUDA;
+    }
+    g_static_addr[dev] = (double*)p;
+  }
+  *out = g_static_addr[dev];
+  return QS_OK;
+}
+
+template <typename A>
+static qs_status marginal_static_impl(const void* state, int N, const int* qubits, int nq, double* out,
+                                      cudaStream_t stream, double* scratch) {
+  MargGeo g;
+  g.N = N; g.nq = nq;
+  int idx[24];
+  for (int m = 0; m < nq; ++m) idx[m] = m;
+  for (int i = 0; i < nq; ++i)
+    for (int j = i + 1; j < nq; ++j)
+      if (qubits[idx[j]] < qubits[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+  uint64_t qmask = 0;
+  for (int m = 0; m < nq; ++m) { g.sq[m] = qubits[idx[m]]; g.outbit[m] = idx[m]; qmask |= 1ull << qubits[m]; }
+  const uint64_t all = (N >= 64) ? ~0ull : ((1ull << N) - 1);
+  g.cmask = all & ~qmask;
+  const int cbits = N - nq;
+  // at most QS_STATIC_PARTIALS partial sums: R * 2^nseg_log <= 2^18
+  int nseg_log = 0;
+  while (nq + nseg_log < 18 && nseg_log < cbits) ++nseg_log;
+  g.nseg_log = nseg_log;
+  g.seglen = 1ull << (cbits - nseg_log);
+  const uint64_t R = 1ull << nq;
+  const uint64_t nthreads = R << nseg_log;
+  double* part = scratch;                       // every entry written by k_marginal
+  double* res = scratch + QS_STATIC_PARTIALS;   // every entry written by k_sum_columns
+  k_marginal<A><<<(unsigned)((nthreads + TPB - 1) / TPB), TPB, 0, stream>>>((const A*)state, g, part, nullptr);
+  QS_LAUNCH_CHECK();
+  k_sum_columns<<<(unsigned)R, TPB, 0, stream>>>(part, 1 << nseg_log, (int)R, res);
+  QS_LAUNCH_CHECK();
+  QS_CUDA(cudaMemcpyAsync(out, res, R * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  QS_CUDA(cudaStreamSynchronize(stream));
+  return QS_OK;
+}
+
+extern "C" qs_status measure_probs_static(const void* state, int N, qs_encoding enc, const int* qubits, int nq,
+                                          double* out, void* cuda_stream) {
+  if (!state || !qubits || !out) { qs_set_error("measure_probs_static: null argument"); return QS_EINVAL; }
+  if (N < 2 || N > 44) { qs_set_error("measure_probs_static: N = %d not in 2..44", N); return QS_EINVAL; }
+  if (enc != QS_C128 && enc != QS_C64) {
+    qs_set_error("measure_probs_static: only QS_C128 and QS_C64 states");
+    return QS_EUNSUPPORTED;
+  }
+  if (nq < 1 || nq > N || nq > QS_STATIC_MAX_NQ) {
+    qs_set_error("measure_probs_static: nq = %d not in 1..min(N, %d): the static scratch holds %d doubles", nq,
+                 QS_STATIC_MAX_NQ, QS_STATIC_SCRATCH_DOUBLES);
+    return QS_EINVAL;
+  }
+  for (int i = 0; i < nq; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= N) { qs_set_error("measure_probs_static: qubit %d out of range", qubits[i]); return QS_EINVAL; }
+    for (int j = 0; j < i; ++j)
+      if (qubits[i] == qubits[j]) { qs_set_error("measure_probs_static: qubit %d repeated", qubits[i]); return QS_EINVAL; }
+  }
+  double* scratch = nullptr;
+  QS_TRY(static_scratch_addr(&scratch));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (enc == QS_C128) return marginal_static_impl<double2>(state, N, qubits, nq, out, st, scratch);
+  return marginal_static_impl<float2>(state, N, qubits, nq, out, st, scratch);
+}

@@ -68,6 +68,7 @@ _SIGS = {
     "sim_norm": (_I, [_P, _D]),
     "expect_xyz": (_I, [_P, _D, _D, _D]),
     "measure_probs": (_I, [_P, _IP, _I, _D]),
+    "measure_probs_static": (_I, [_P, _I, _I, _IP, _I, _D, _P]),
     "sim_copy_out": (_I, [_P, _P, ctypes.c_size_t, _D]),
     "sim_copy_in": (_I, [_P, _P, ctypes.c_size_t, _D]),
     "sim_sync": (_I, [_P]),
@@ -308,6 +309,16 @@ class Sim:
             raise ValueError("need %d bytes" % self.nbytes)
         r = np.asarray(r0r1 if r0r1 is not None else (0.0, 0.0), dtype=np.float64)
         _check(_lib.sim_copy_in(self._h, _P(a.ctypes.data), self.nbytes, r.ctypes.data_as(_D)))
+
+
+def measure_probs_static(state_ptr, N, enc, qubits, stream=0):
+    """measure_probs on a caller-held device state without any allocation
+    (the library's fixed scratch; see include/qsim.h)."""
+    q, nq = _ints(qubits)
+    out = np.empty(1 << nq)
+    e = ENCODINGS[enc] if isinstance(enc, str) else int(enc)
+    _check(_lib.measure_probs_static(_P(state_ptr), int(N), e, q, nq, out.ctypes.data_as(_D), _P(int(stream))))
+    return out
 
 
 def _mat8(U):
