@@ -54,6 +54,7 @@ struct TileParams2 {
   uint8_t gpos[20];    // global position of local bit k
   TMap init, fin;      // register / warp assignment at load and at store
   int nops;
+  int last_xpose;      // index of the last transpose op, -1 if none
   TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
   TMap maps[16];
 };
@@ -117,6 +118,15 @@ __device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) 
 // skip0 / skip1 leave the elements with a unit factor untouched
 template <typename R, int RB, int S>
 __device__ __forceinline__ void reg_diag(Cx<R>* v, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
+  if (smask == 0) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+      const bool one = (j >> S) & 1;
+      if (one ? skip1 : skip0) continue;
+      v[j] = cmul_code(v[j], one ? d1 : d0, 4);
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < (1 << RB); ++j) {
     if ((j & (int)smask) != (int)smask) continue;
@@ -156,12 +166,21 @@ template <> __device__ __forceinline__ float shx<float>(float x, int m) { return
 template <> __device__ __forceinline__ double shx<double>(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
 
 // lane-bit op: partner values by shuffle, each lane keeps its own output
-template <typename R, int RB>
+template <typename R, int RB, bool SWAP>
 __device__ __forceinline__ void lane_op(Cx<R>* v, const TOp& o, int lane, bool tok) {
   const int m = 1 << o.a;
   const bool hi = (lane >> o.a) & 1;
   Cx<R> u00 = ucx<R>(o, 0), u01 = ucx<R>(o, 1), u10 = ucx<R>(o, 2), u11 = ucx<R>(o, 3);
   if constexpr (sizeof(R) == 4) {
+    if (SWAP && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) {
+      // pure swap: every lane takes its partner's value
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (tok && (j & (int)o.smask) == (int)o.smask) v[j] = p;
+      }
+      return;
+    }
     // each lane keeps cs * own + cp * partner, with per-lane coefficients
     const Cx<R> cs = hi ? u11 : u00, cp = hi ? u10 : u01;
     if (o.smask == 0) {
@@ -243,14 +262,64 @@ __device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t bas
   }
 }
 
+// FEAT: which specialised complex64 paths the pass needs (bit 0: swaps, bit 1:
+// Hadamard-shaped); passes without them run a smaller kernel.
+constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;
+
+// 16-byte global -> shared copies that bypass registers (LDGSTS), so the next
+// tile's loads are in flight while the current tile is computed and stored.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Each thread stages exactly the 16-byte chunks it will read back, so the
+// stage buffer needs no barrier: the thread's own wait_group orders it.
 template <typename R, int RB>
+__device__ __forceinline__ void stage_tile(const void* s, Cx<R>* st, uint64_t base, const uint64_t* roff, uint64_t woff,
+                                           const TMap& m, uint32_t tl) {
+#pragma unroll
+  for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
+    const uint64_t g = base + woff + roff[jj];
+    if constexpr (sizeof(R) == 4) {
+      cp_async16(((float4*)st) + (l >> 1), ((const float4*)s) + (g >> 1));
+    } else {
+      cp_async16(st + l, ((const double2*)s) + g);
+      cp_async16(st + l + 1, ((const double2*)s) + g + 1);
+    }
+  }
+  cp_async_commit();
+}
+template <typename R, int RB>
+__device__ __forceinline__ void unstage_tile(const Cx<R>* st, Cx<R>* v, const TMap& m, uint32_t tl) {
+#pragma unroll
+  for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
+    if constexpr (sizeof(R) == 4) {
+      const float4 x = ((const float4*)st)[l >> 1];
+      v[2 * jj] = cx<float>(x.x, x.y);
+      v[2 * jj + 1] = cx<float>(x.z, x.w);
+    } else {
+      v[2 * jj] = st[l];
+      v[2 * jj + 1] = st[l + 1];
+    }
+  }
+}
+
+template <typename R, int RB, int FEAT>
 __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __grid_constant__ TileParams2 P) {
   extern __shared__ unsigned char smraw[];
   constexpr int NR = 1 << RB;
   // global offsets of the register part (pairs jj: slots 1..RB-1) at load / store
   uint64_t* roff_in = (uint64_t*)smraw;
   uint64_t* roff_out = roff_in + NR / 2;
-  Cx<R>* xb = (Cx<R>*)(smraw + NR * sizeof(uint64_t));  // transpose buffer, 2^b elements
+  // transpose buffer, 2^b elements; between the last transpose of a tile and
+  // the start of the next it stages the next tile
+  Cx<R>* xb = (Cx<R>*)(smraw + NR * sizeof(uint64_t));
+  Cx<R>* stg = xb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < NR / 2) {
     roff_in[threadIdx.x] = goff(lidx<RB>(P.init, 2 * threadIdx.x, 0), P.gpos, P.b);
@@ -259,13 +328,20 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
   __syncthreads();
   const uint64_t woff_in = goff(thread_part(P.init, lane, warp), P.gpos, P.b);
   const uint64_t woff_out = goff(thread_part(P.fin, lane, warp), P.gpos, P.b);
+  const uint32_t tl_in = thread_part(P.init, lane, warp);
   const uint64_t ntiles = 1ull << (P.N - P.b);
   Cx<R> v[NR];
+  if (blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
     const uint64_t base = deposit_t(tau, P.out_mask);
-    load_tile<R, RB>(s, v, base, roff_in, woff_in, lane);
+    cp_async_wait_all();
+    unstage_tile<R, RB>(stg, v, P.init, tl_in);
+    const uint64_t nxt = tau + gridDim.x;
+    if (P.last_xpose < 0 && nxt < ntiles)
+      stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
     TMap cur = P.init;
     uint32_t tl = thread_part(cur, lane, warp);
+    Cx<R> fac = cx<R>((R)1, (R)0);
     int mapi = 0;
     for (int i = 0; i < P.nops; ++i) {
       const TOp& o = P.ops[i];
@@ -297,19 +373,43 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
           }
         }
         __syncthreads();
+        if (i == P.last_xpose && nxt < ntiles)
+          stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
         continue;
       }
-      if ((base & o.gmask) != o.gmask) continue;          // an outer control is 0
+      const bool gok = (base & o.gmask) == o.gmask;       // outer controls
       const bool tok = (tl & o.tmask) == o.tmask;         // lane / warp controls
+      if (o.pad[0] != 0) {
+        // folded run of per-thread diagonals: multiply the factor, apply at the end
+        if (gok && tok) {
+          const bool one = (o.type == T_DIAG_THR) ? ((tl >> o.a) & 1) : ((base & o.gtbit) != 0);
+          if ((one ? o.c1 : o.c0) != 0) fac = cmul_code(fac, ucx<R>(o, one ? 3 : 0), 4);
+        }
+        if (o.pad[0] == 2) {
+          if (fac.x != (R)1 || fac.y != (R)0) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) v[j] = cmul_code(v[j], fac, 4);
+          }
+          fac = cx<R>((R)1, (R)0);
+        }
+        continue;
+      }
+      if (!gok) continue;
       switch (o.type) {
         case T_REG: {
           if (!tok) break;
           if constexpr (sizeof(R) == 4) {
-            // complex64: every non-diagonal gate as a dense 2x2 (exact for the
-            // unit entries of X / Y / CNOT / TOFFOLI); one code path keeps the
-            // kernel small
-            OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
-            reg_op<R, RB>(v, o.a, o.smask, f);
+            // complex64: Hadamard-shaped or dense (exact for the unit entries
+            // of X, Y, CNOT, TOFFOLI)
+            // (a register-slot swap as renames makes the register allocation
+            // spill at 128 registers; swaps on register slots stay dense)
+            if ((FEAT & FEAT_HAD) && o.kind == GK_HAD) {
+              OpHad<R> f; f.s = uscal<R>(o);
+              reg_op<R, RB>(v, o.a, o.smask, f);
+            } else {
+              OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
+              reg_op<R, RB>(v, o.a, o.smask, f);
+            }
           } else {
             // complex128: the FP64 pipe is the bound, so keep the cheaper forms
             switch (o.kind) {
@@ -324,7 +424,7 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
           break;
         }
         case T_LANE:
-          lane_op<R, RB>(v, o, lane, tok);
+          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0>(v, o, lane, tok);
           break;
         case T_DIAG_REG:
         case T_DIAG_THR:
@@ -348,9 +448,14 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
             const int code = one ? o.c1 : o.c0;
             if (code == 0) break;
             const Cx<R> d = one ? d1 : d0;
+            if (o.smask == 0) {
 #pragma unroll
-            for (int j = 0; j < NR; ++j)
-              if ((j & (int)o.smask) == (int)o.smask) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
+              for (int j = 0; j < NR; ++j) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
+            } else {
+#pragma unroll
+              for (int j = 0; j < NR; ++j)
+                if ((j & (int)o.smask) == (int)o.smask) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
+            }
           }
           break;
         }
@@ -374,30 +479,116 @@ static void fill_u(TOp& o, const double* u) {
   for (int k = 0; k < 8; ++k) { o.ud[k] = u[k]; o.uf[k] = (float)u[k]; }
 }
 
+// ---- gate-sequence rewriting inside a pass (exact up to rounding) ----------------
+static bool same_controls(const qs_gate& a, const qs_gate& b) {
+  if (a.nc != b.nc) return false;
+  if (a.nc == 0) return true;
+  if (a.nc == 1) return a.controls[0] == b.controls[0];
+  return (a.controls[0] == b.controls[0] && a.controls[1] == b.controls[1]) ||
+         (a.controls[0] == b.controls[1] && a.controls[1] == b.controls[0]);
+}
+static bool is_diag_gate(const qs_gate& g) { return classify_u2(g.u).kind == GK_DIAG; }
+// u = b * a (apply a first), 2x2 complex row-major (re, im)
+static void mat_mul2(const double* b, const double* a, double* u) {
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) {
+      double re = 0, im = 0;
+      for (int k = 0; k < 2; ++k) {
+        const double br = b[2 * (2 * r + k)], bi = b[2 * (2 * r + k) + 1];
+        const double ar = a[2 * (2 * k + c)], ai = a[2 * (2 * k + c) + 1];
+        re += br * ar - bi * ai;
+        im += br * ai + bi * ar;
+      }
+      u[2 * (2 * r + c)] = re;
+      u[2 * (2 * r + c) + 1] = im;
+    }
+}
+// Diagonal gates commute with each other and with every gate whose target is
+// none of their qubits (a control acts diagonally too), so each diagonal gate
+// is delayed until a non-diagonal gate targets its target or one of its
+// controls, or the pass ends; the delayed gates are emitted together.  Then neighbouring gates with the same
+// target and the same controls are multiplied into one 2x2 (FP64, host).
+static int rewrite_pass(const qs_gate* gates, const int* gidx, int ng, qs_gate* out) {
+  int n = 0;
+  int pend[MAX_TOPS * 2];
+  int np = 0;
+  for (int i = 0; i < ng; ++i) {
+    const qs_gate& g = gates[gidx[i]];
+    if (is_diag_gate(g)) { pend[np++] = gidx[i]; continue; }
+    // a delayed diagonal must not pass a gate whose target is one of its
+    // qubits (its target or one of its controls)
+    bool conflict = false;
+    for (int k = 0; k < np; ++k) {
+      const qs_gate& d = gates[pend[k]];
+      conflict |= (d.target == g.target);
+      for (int c = 0; c < d.nc; ++c) conflict |= (d.controls[c] == g.target);
+    }
+    if (conflict) {
+      for (int k = 0; k < np; ++k) out[n++] = gates[pend[k]];
+      np = 0;
+    }
+    out[n++] = g;
+  }
+  for (int k = 0; k < np; ++k) out[n++] = gates[pend[k]];
+  // compose neighbours with equal (target, controls)
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    if (m > 0 && out[m - 1].target == out[i].target && same_controls(out[m - 1], out[i])) {
+      double u[8];
+      mat_mul2(out[i].u, out[m - 1].u, u);
+      memcpy(out[m - 1].u, u, sizeof u);
+      continue;
+    }
+    out[m++] = out[i];
+  }
+  return m;
+}
+
 // Build the op list of one pass.  tile: bitmask of the tile's global bits
 // (contains bits 0..5), gidx: the gates in order.  Returns false if the op
 // list overflows (caller splits the pass).
-static bool build_pass(const qs_gate* gates, const int* gidx, int ng, int N, int b, int RB, uint64_t tile,
+static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, int N, int b, int RB, uint64_t tile,
                        TileParams2* P) {
+  static thread_local qs_gate seq[MAX_TOPS * 2];
+  static thread_local int seq_idx[MAX_TOPS * 2];
+  if (ng_in > MAX_TOPS * 2) return false;
+  const int ng = rewrite_pass(gates_in, gidx_in, ng_in, seq);
+  for (int i = 0; i < ng; ++i) seq_idx[i] = i;
+  const qs_gate* gates = seq;
+  const int* gidx = seq_idx;
   memset(P, 0, sizeof *P);
   P->N = N;
   P->b = b;
   // local bits: 0..3 = index bits 0..3 (runs of 16 amplitudes), 4..5 = the
   // two high tile qubits with the fewest non-diagonal gates in the pass
   // (lane qubits, updated by shuffles), 6..b-1 = the other tile qubits
+  // Lane score: a swap (X, CNOT, TOFFOLI) on a lane qubit costs two shuffles
+  // and no arithmetic, a dense gate there costs the shuffles on top of the
+  // arithmetic it costs anyway; prefer swap-heavy, dense-light lane qubits.
   int local[64];
   int uses[64];
   for (int q = 0; q < 64; ++q) { local[q] = -1; uses[q] = 0; }
   for (int i = 0; i < ng; ++i) {
     const qs_gate& g = gates[gidx[i]];
-    if (classify_u2(g.u).kind != GK_DIAG) uses[g.target]++;
+    GateClass gc = classify_u2(g.u);
+    if (gc.kind == GK_DIAG) continue;
+    const bool swap = (gc.kind == GK_ANTI && gc.c0 == 0 && gc.c1 == 0);
+    uses[g.target] += swap ? -4 : 1;
   }
   for (int q = 0; q < LOW_BITS; ++q) { P->gpos[q] = (uint8_t)q; local[q] = q; }
   int k = LOW_BITS;
+  int is_target[64];
+  for (int q = 0; q < 64; ++q) is_target[q] = 0;
+  for (int i = 0; i < ng; ++i)
+    if (classify_u2(gates[gidx[i]].u).kind != GK_DIAG) is_target[gates[gidx[i]].target] = 1;
   for (int pick = 0; pick < 2; ++pick) {
+    // lane qubits: targets first (so the rest fit the register slots), by score
     int best = -1;
-    for (int q = LOW_BITS; q < N; ++q)
-      if (((tile >> q) & 1) && local[q] < 0 && (best < 0 || uses[q] < uses[best])) best = q;
+    for (int q = LOW_BITS; q < N; ++q) {
+      if (!((tile >> q) & 1) || local[q] >= 0) continue;
+      if (best < 0 || is_target[q] > is_target[best] || (is_target[q] == is_target[best] && uses[q] < uses[best]))
+        best = q;
+    }
     P->gpos[k] = (uint8_t)best;
     local[best] = k++;
   }
@@ -492,8 +683,42 @@ static bool build_pass(const qs_gate* gates, const int* gidx, int ng, int N, int
     }
     P->ops[nops++] = o;
   }
+  // diagonal ops commute: inside each run of them, put the register-slot ones
+  // first so that the per-thread ones are contiguous
+  for (int i = 0; i < nops;) {
+    auto isd = [&](int k) {
+      const int t = P->ops[k].type;
+      return t == T_DIAG_REG || t == T_DIAG_THR || t == T_DIAG_OUT;
+    };
+    int j = i;
+    while (j < nops && isd(j)) ++j;
+    if (j - i >= 2) {
+      TOp tmp[MAX_TOPS];
+      int m = 0;
+      for (int k = i; k < j; ++k)
+        if (P->ops[k].type == T_DIAG_REG || P->ops[k].smask != 0) tmp[m++] = P->ops[k];
+      for (int k = i; k < j; ++k)
+        if (!(P->ops[k].type == T_DIAG_REG || P->ops[k].smask != 0)) tmp[m++] = P->ops[k];
+      for (int k = 0; k < m; ++k) P->ops[i + k] = tmp[k];
+    }
+    i = (j > i) ? j : i + 1;
+  }
+  // runs of per-thread diagonals (target on a lane / warp bit or outside the
+  // tile, no register-slot control) fold into one factor per thread
+  for (int i = 0; i < nops;) {
+    int j = i;
+    while (j < nops && (P->ops[j].type == T_DIAG_THR || P->ops[j].type == T_DIAG_OUT) && P->ops[j].smask == 0) ++j;
+    if (j - i >= 2) {
+      for (int k = i; k < j - 1; ++k) P->ops[k].pad[0] = 1;  // accumulate
+      P->ops[j - 1].pad[0] = 2;                              // accumulate and apply
+    }
+    i = (j > i) ? j : i + 1;
+  }
   P->nops = nops;
   P->fin = cur;
+  P->last_xpose = -1;
+  for (int i = 0; i < nops; ++i)
+    if (P->ops[i].type == T_XPOSE) P->last_xpose = i;
   return true;
 }
 
@@ -511,11 +736,21 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
   int* gidx = (int*)malloc(sizeof(int) * (size_t)(n + 1));
   if (!gidx) return QS_ENOMEM;
   const uint64_t low = (1ull << LOW_BITS) - 1;
+  // A transpose costs about a third of a sweep, so a pass takes only as many
+  // high targets as the lanes and register slots hold (no transposes); the
+  // warp bits are padding.
+  const int max_targets = LOW_BITS + 2 + (tile_register_bits(s->enc) - 1);
   uint64_t S = low;
   int ng = 0, launched = 0;
   qs_status st = QS_OK;
   auto flush = [&](uint64_t tile) -> qs_status {
-    // pad the tile to b bits with the lowest unused bits
+    // pad the tile to b bits: first with qubits the pass's diagonal gates or
+    // controls use (they become thread-uniform), then the lowest unused bits
+    for (int k = 0; k < ng && __builtin_popcountll(tile) < b; ++k) {
+      const qs_gate& g = gates[gidx[k]];
+      if (classify_u2(g.u).kind == GK_DIAG) tile |= 1ull << g.target;
+      for (int c = 0; c < g.nc && __builtin_popcountll(tile) < b; ++c) tile |= 1ull << g.controls[c];
+    }
     for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
     return run_pass(s, gates, gidx, ng, tile, &launched, timer);
   };
@@ -524,7 +759,7 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
     if (gc.kind == GK_IDENT) continue;
     uint64_t need = (gc.kind == GK_DIAG) ? 0ull : (1ull << gates[i].target);
     uint64_t S2 = S | need;
-    if ((__builtin_popcountll(S2) > b || ng >= MAX_TOPS / 2) && ng > 0) {
+    if ((__builtin_popcountll(S2) > max_targets || ng >= MAX_TOPS / 2) && ng > 0) {
       st = flush(S);
       ng = 0;
       S = low | need;
@@ -543,16 +778,31 @@ static qs_status launch_pass(qs_sim* s, const TileParams2& P, PassTimer* timer) 
   const bool timed = timer && timer->n < timer->max_ev;
   if (timed) QS_CUDA(cudaEventRecord(timer->ev[2 * timer->n], s->stream));
   const uint64_t ntiles = 1ull << (s->N - P.b);
-  const uint64_t gmax = (uint64_t)s->num_sms * 4;
+  const uint64_t gmax = (uint64_t)s->num_sms * 2;   // two persistent CTAs per SM
   const unsigned grid = (unsigned)(ntiles < gmax ? ntiles : gmax);
   if (s->enc == QS_C128) {
     const size_t smem = ((size_t)16 << P.b) + 16 * sizeof(uint64_t);
-    QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tile2<double, 4><<<grid, TPB, smem, s->stream>>>(s->state, P);
+    QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
   } else {
+    int feat = 0;
+    for (int i = 0; i < P.nops; ++i) {
+      const TOp& o = P.ops[i];
+      if (o.type == T_LANE && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) feat |= FEAT_SWAP;
+      if (o.type == T_REG && o.kind == GK_HAD) feat |= FEAT_HAD;
+    }
     const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
-    QS_CUDA(cudaFuncSetAttribute(k_tile2<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tile2<float, 5><<<grid, TPB, smem, s->stream>>>(s->state, P);
+    auto go = [&](auto kern) -> qs_status {
+      QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, TPB, smem, s->stream>>>(s->state, P);
+      return QS_OK;
+    };
+    switch (feat) {
+      case 0: QS_TRY(go(k_tile2<float, 5, 0>)); break;
+      case 1: QS_TRY(go(k_tile2<float, 5, 1>)); break;
+      case 2: QS_TRY(go(k_tile2<float, 5, 2>)); break;
+      default: QS_TRY(go(k_tile2<float, 5, 3>)); break;
+    }
   }
   QS_LAUNCH_CHECK();
   if (timed) {
