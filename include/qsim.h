@@ -215,6 +215,41 @@ qs_status measure_probs(qs_sim* sim, const int* qubits, int nq, double* out);
 qs_status measure_probs_static(const void* state, int N, qs_encoding enc, const int* qubits, int nq,
                                double* out, void* cuda_stream);
 
+/* ---- batched small states ------------------------------------------------- */
+/* Many independent N-qubit states advanced through their own gate lists in
+ * one launch (each gate is the pair update of Eq. (NUM2) / Eq. (AQS0); the
+ * batching itself has no counterpart in the paper).  Every state is held in
+ * on-chip shared memory for its whole gate list, so one launch reads and
+ * writes each state once.  QS_C64 (2 <= N <= 14) or QS_C128 (2 <= N <= 13);
+ * the states live in one device allocation owned by the handle, state s at
+ * element offset s * 2^N, each starting as |0..0>. */
+typedef struct qs_batch qs_batch;
+qs_status batch_create(int N, qs_encoding enc, int nstates, void* cuda_stream, qs_batch** out);
+qs_status batch_destroy(qs_batch* b);
+/* Every state back to |0..0>. */
+qs_status batch_reset(qs_batch* b);
+/* Gate lists: state s runs gates[offsets[s] .. offsets[s+1]-1] (host arrays;
+ * offsets has nstates + 1 non-decreasing entries starting at 0).  Validated
+ * like circuit_run; copied to the device (the host arrays may be freed). */
+qs_status batch_set_circuits(qs_batch* b, const qs_gate* gates, const int* offsets);
+/* Advance every state through its gate list: one kernel launch, or the
+ * captured CUDA graph when batch_capture was called. */
+qs_status batch_run(qs_batch* b);
+/* Capture one batch_run into a CUDA graph that later batch_run calls replay. */
+qs_status batch_capture(qs_batch* b);
+/* Time the launch layouts (one CTA per state, one warp per state for N <= 9)
+ * and CTA sizes on the current gate lists and keep the fastest; the states
+ * are restored afterwards.  Outputs may be NULL. */
+qs_status batch_autotune(qs_batch* b, int* layout, int* threads, float* best_ms);
+/* <Phi|Phi> of every state (host, nstates doubles), FP64. */
+qs_status batch_norms(qs_batch* b, double* out);
+/* Raw amplitudes of all states (nstates * 2^N * 8 or 16 bytes), host. */
+qs_status batch_copy_out(qs_batch* b, void* host, size_t bytes);
+qs_status batch_copy_in(qs_batch* b, const void* host, size_t bytes);
+/* Current layout (0: CTA per state, 1: warp per state), CTA size and the
+ * device address of the states. */
+qs_status batch_info(const qs_batch* b, int* layout, int* threads, void** dev_states);
+
 /* ---- raw state access (parity dumps) ------------------------------------- */
 /* Copy the raw amplitudes (2^N * bytes-per-amplitude bytes, layout as in
  * qs_encoding) to / from host memory.  For QS_ADAPT2, r0r1 (host, 2 doubles,

@@ -72,6 +72,17 @@ _SIGS = {
     "sim_copy_out": (_I, [_P, _P, ctypes.c_size_t, _D]),
     "sim_copy_in": (_I, [_P, _P, ctypes.c_size_t, _D]),
     "sim_sync": (_I, [_P]),
+    "batch_create": (_I, [_I, _I, _I, _P, ctypes.POINTER(_P)]),
+    "batch_destroy": (_I, [_P]),
+    "batch_reset": (_I, [_P]),
+    "batch_set_circuits": (_I, [_P, ctypes.POINTER(qs_gate), _IP]),
+    "batch_run": (_I, [_P]),
+    "batch_capture": (_I, [_P]),
+    "batch_autotune": (_I, [_P, _IP, _IP, ctypes.POINTER(ctypes.c_float)]),
+    "batch_norms": (_I, [_P, _D]),
+    "batch_copy_out": (_I, [_P, _P, ctypes.c_size_t]),
+    "batch_copy_in": (_I, [_P, _P, ctypes.c_size_t]),
+    "batch_info": (_I, [_P, _IP, _IP, ctypes.POINTER(_P)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -309,6 +320,84 @@ class Sim:
             raise ValueError("need %d bytes" % self.nbytes)
         r = np.asarray(r0r1 if r0r1 is not None else (0.0, 0.0), dtype=np.float64)
         _check(_lib.sim_copy_in(self._h, _P(a.ctypes.data), self.nbytes, r.ctypes.data_as(_D)))
+
+
+class Batch:
+    """nstates independent N-qubit states advanced in one launch (see
+    include/qsim.h, batched small states)."""
+
+    def __init__(self, N, enc, nstates, stream=None):
+        import torch
+        self.N, self.nstates = int(N), int(nstates)
+        self.enc = ENCODINGS[enc] if isinstance(enc, str) else int(enc)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream_handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = _P()
+        _check(_lib.batch_create(self.N, self.enc, self.nstates, _P(self.stream_handle), ctypes.byref(h)))
+        self._h = h
+        self.nbytes = (self.nstates << self.N) * AMP_BYTES[self.enc]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_lib.batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        _check(_lib.batch_reset(self._h))
+
+    def set_circuits(self, circuits):
+        """circuits: one list of gate records per state."""
+        recs = [r for c in circuits for r in c]
+        arr, n = gate_array(recs)
+        offs = np.zeros(self.nstates + 1, dtype=np.int32)
+        offs[1:] = np.cumsum([len(c) for c in circuits])
+        o = (ctypes.c_int * (self.nstates + 1))(*offs.tolist())
+        _check(_lib.batch_set_circuits(self._h, arr, o))
+
+    def run(self):
+        _check(_lib.batch_run(self._h))
+
+    def capture(self):
+        _check(_lib.batch_capture(self._h))
+
+    def autotune(self):
+        lay, th, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0)
+        _check(_lib.batch_autotune(self._h, ctypes.byref(lay), ctypes.byref(th), ctypes.byref(ms)))
+        return lay.value, th.value, ms.value
+
+    def info(self):
+        lay, th, p = ctypes.c_int(0), ctypes.c_int(0), _P()
+        _check(_lib.batch_info(self._h, ctypes.byref(lay), ctypes.byref(th), ctypes.byref(p)))
+        return lay.value, th.value, p.value
+
+    def norms(self):
+        out = np.empty(self.nstates)
+        _check(_lib.batch_norms(self._h, out.ctypes.data_as(_D)))
+        return out
+
+    def copy_out(self):
+        dt = np.complex128 if self.enc == C128 else np.complex64
+        a = np.empty(self.nstates << self.N, dtype=dt)
+        _check(_lib.batch_copy_out(self._h, _P(a.ctypes.data), self.nbytes))
+        return a.reshape(self.nstates, 1 << self.N)
+
+    def copy_in(self, a):
+        dt = np.complex128 if self.enc == C128 else np.complex64
+        a = np.ascontiguousarray(a, dtype=dt)
+        _check(_lib.batch_copy_in(self._h, _P(a.ctypes.data), self.nbytes))
 
 
 def measure_probs_static(state_ptr, N, enc, qubits, stream=0):

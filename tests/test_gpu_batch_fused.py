@@ -1,0 +1,101 @@
+"""GPU parity of the batched small-state path and of the dense fused k-qubit
+gate against the oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import circuit, statevec as sv  # noqa: E402
+from paper_1805_04708_gb300 import workloads as wl  # noqa: E402
+
+TOL = {"c128": 1e-12, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_1805_04708_gb300 import build
+    build.build()
+    from paper_1805_04708_gb300 import qsim
+    torch.cuda.set_device(0)
+    return qsim
+
+
+def haar(n, seed):
+    g = np.random.default_rng(seed)
+    Z = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    Q, R = np.linalg.qr(Z)
+    return Q * (np.diag(R) / np.abs(np.diag(R)))
+
+
+@pytest.mark.parametrize("enc,N", [("c64", 4), ("c64", 9), ("c64", 12), ("c64", 14),
+                                   ("c128", 5), ("c128", 9), ("c128", 13)])
+def test_batch_matches_oracle(q, enc, N):
+    ns = 37 if N <= 12 else 9
+    circs = [wl.random_mixed_circuit(N, 5 + 7 * (s % 5), seed=1000 * N + s) for s in range(ns)]
+    with q.Batch(N, enc, ns) as b:
+        b.set_circuits(circs)
+        b.run()
+        got = b.copy_out()
+        nrm = b.norms()
+    for s in range(ns):
+        ref = circuit.run(sv.zero_state(N), N, circs[s])
+        assert np.max(np.abs(got[s] - ref)) <= TOL[enc], s
+        assert abs(nrm[s] - sv.norm(got[s].astype(np.complex128))) <= 1e-12
+
+
+@pytest.mark.parametrize("enc,N", [("c64", 7), ("c64", 11), ("c128", 10)])
+def test_batch_graph_and_autotune(q, enc, N):
+    ns = 64
+    circs = [wl.layered_circuit(N, 2, seed=s) for s in range(ns)]
+    with q.Batch(N, enc, ns) as b:
+        b.set_circuits(circs)
+        layout, threads, ms = b.autotune()
+        assert layout in (0, 1) and threads in (64, 128, 256, 512, 1024) and ms > 0
+        assert b.info()[:2] == (layout, threads)
+        b.capture()
+        b.run()          # graph replay: one pass of every circuit
+        b.run()          # and a second one
+        got = b.copy_out()
+    for s in range(0, ns, 7):
+        ref = circuit.run(sv.zero_state(N), N, circs[s] + circs[s])
+        assert np.max(np.abs(got[s] - ref)) <= TOL[enc] * 2
+
+
+def test_batch_errors(q):
+    with pytest.raises(q.QSError):
+        q.Batch(15, "c64", 4)
+    with q.Batch(4, "c64", 2) as b:
+        with pytest.raises(q.QSError):
+            b.set_circuits([[("H", (4,), ())], []])
+        with pytest.raises(q.QSError):
+            b.set_circuits([[("CNOT", (1, 1), ())], []])
+
+
+@pytest.mark.parametrize("enc", ["c128", "c64"])
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_apply_fused_dense(q, enc, k):
+    N = 11
+    g = np.random.default_rng(k)
+    v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
+    v0 /= np.linalg.norm(v0)
+    with q.Sim(N, enc) as s:
+        s.copy_in(v0)
+        ref = v0.astype(np.complex64).astype(np.complex128) if enc == "c64" else v0.copy()
+        for trial in range(3):
+            qubits = [int(x) for x in g.choice(N, k, replace=False)]
+            U = haar(1 << k, 10 * k + trial)
+            s.apply_fused(qubits, U)
+            sv.apply_dense(ref, N, qubits, U)
+        got = s.copy_out()
+    assert np.max(np.abs(got - ref)) <= TOL[enc] * (4 if enc == "c64" and k == 5 else 1)
+
+
+def test_apply_fused_rejects(q):
+    with q.Sim(6, "c128") as s:
+        with pytest.raises(q.QSError) as e:
+            s.apply_fused([0, 1], np.ones((4, 4)))
+        assert e.value.name == "QS_ENOTUNITARY"
+        with pytest.raises(q.QSError):
+            s.apply_fused([0, 0], np.eye(4))
