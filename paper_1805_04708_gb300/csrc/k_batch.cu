@@ -273,12 +273,23 @@ extern "C" qs_status batch_capture(qs_batch* b) {
   if (!b->gates) { qs_set_error("batch_capture: no circuits set"); return QS_EINVAL; }
   if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
-  QS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  qs_status st = launch_batch(b, b->layout, b->threads);
+  // capture on a private stream (the legacy default stream cannot be
+  // captured); the graph is later launched on the handle's stream
+  cudaStream_t cs = nullptr;
+  QS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t user = b->stream;
+  b->stream = cs;
+  cudaError_t e0 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  qs_status st = (e0 == cudaSuccess) ? launch_batch(b, b->layout, b->threads) : QS_ECUDA;
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-  if (st != QS_OK) { if (g) cudaGraphDestroy(g); return st; }
-  if (e != cudaSuccess) { qs_set_error("batch_capture: %s", cudaGetErrorString(e)); return QS_ECUDA; }
+  cudaError_t e = (e0 == cudaSuccess) ? cudaStreamEndCapture(cs, &g) : e0;
+  b->stream = user;
+  cudaStreamDestroy(cs);
+  if (st != QS_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st == QS_OK) qs_set_error("batch_capture: %s", cudaGetErrorString(e));
+    return st != QS_OK ? st : QS_ECUDA;
+  }
   b->graph = g;
   QS_CUDA(cudaGraphInstantiate(&b->gexec, g, 0));
   return QS_OK;
