@@ -250,6 +250,45 @@ qs_status batch_copy_in(qs_batch* b, const void* host, size_t bytes);
  * device address of the states. */
 qs_status batch_info(const qs_batch* b, int* layout, int* threads, void** dev_states);
 
+/* ---- serving loop ---------------------------------------------------------- */
+/* A stream of requests (circuits of mixed qubit counts, complex64 storage,
+ * FP64 results) served with continuous batching: the oldest waiting request
+ * is admitted as soon as its state fits the device-memory budget (admission
+ * by HBM footprint); every admitted request advances by up to `quantum` gates
+ * per scheduling tick -- all small states (N <= small_max_n <= 14) together in
+ * one launch that keeps each state on chip for its gate chunk, larger states
+ * through the tile planner on their own streams, overlapping on the device;
+ * finished requests are retired and their memory reused.  Each gate is the
+ * pair update of Eq. (NUM2); serving has no counterpart in the paper. */
+typedef struct {
+  double arrival_s;       /* in: arrival, seconds after serve_run starts (non-decreasing) */
+  int N;                  /* in: qubits, 2..34 */
+  int ngates;             /* in */
+  const qs_gate* gates;   /* in: host, ngates records, must stay valid during serve_run */
+  double* qz;             /* out: host, N doubles: P(qubit n = 1) of the final state */
+  double norm;            /* out: <Phi|Phi> of the final state (FP64) */
+  double admit_s;         /* out: admission time (seconds after start) */
+  double finish_s;        /* out: completion time (seconds after start) */
+} qs_request;
+typedef struct {
+  size_t mem_budget;      /* bytes of device memory for resident states and gate lists */
+  int quantum;            /* gates per request per tick (<= 0: 64) */
+  int max_small;          /* small states per batched launch (<= 0: 4096) */
+  int nstreams;           /* streams for larger states (<= 0: 4, at most 16) */
+  int small_max_n;        /* largest N of the batched path (<= 0: 14) */
+} qs_serve_config;
+typedef struct {
+  int completed, ticks, max_active;
+  double wall_s;          /* from start to the last completion */
+  double busy_s;          /* time spent in ticks (at least one request active) */
+  uint64_t launches;      /* kernels launched */
+  size_t peak_bytes;      /* peak pool usage */
+} qs_serve_stats;
+/* Serve n requests (sorted by arrival) in real time on the current device.
+ * Rejects malformed requests and requests that cannot fit the budget before
+ * anything runs.  Allocates the budget once (plus small staging buffers). */
+qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* cfg, qs_serve_stats* stats);
+
 /* ---- raw state access (parity dumps) ------------------------------------- */
 /* Copy the raw amplitudes (2^N * bytes-per-amplitude bytes, layout as in
  * qs_encoding) to / from host memory.  For QS_ADAPT2, r0r1 (host, 2 doubles,

@@ -1,0 +1,320 @@
+// Serving loop with continuous batching (native scheduler).
+//
+// Requests (circuits of mixed qubit counts) arrive over time.  The loop
+//  * admits the oldest waiting request once its state fits the device-memory
+//    budget (first-fit allocator over one pooled allocation: admission by HBM
+//    footprint), so requests join while others are in flight;
+//  * advances every admitted request by up to `quantum` gates per tick:
+//    small states (N <= small_max_n) all together in ONE launch that holds
+//    each state in shared memory for its gate chunk (a new request starts
+//    from |0..0> inside that launch, a finishing one computes its norm and
+//    P(qubit = 1) there too); larger states run their chunk through the tile
+//    planner on their own streams, so their work overlaps on the device;
+//  * retires finished requests, frees their memory and records times.
+// Each gate is the pair update of Eq. (NUM2); serving itself has no
+// counterpart in the paper.
+#include "internal.cuh"
+#include "cplx.cuh"
+#include "batch_common.cuh"
+#include <chrono>
+#include <map>
+#include <vector>
+#include <algorithm>
+#include <stdlib.h>
+#include <string.h>
+#include <thread>
+
+namespace {
+
+constexpr int STPB = 256;
+
+struct SmallEntry {
+  float2* state;          // device
+  const BGate<float>* gates;  // device, the request's whole gate list
+  int N, g0, g1;          // gate range for this tick
+  int fresh;              // start from |0..0>
+  int final_;             // compute results after the chunk
+  double* out;            // device: [norm, P1(0..N-1)]
+};
+
+__global__ void __launch_bounds__(STPB) k_serve_small(const SmallEntry* __restrict__ tab) {
+  extern __shared__ unsigned char smraw[];
+  Cx<float>* st = (Cx<float>*)smraw;
+  __shared__ double red[32];
+  const SmallEntry e = tab[blockIdx.x];
+  const int n = 1 << e.N;
+  if (e.fresh) {
+    for (int i = threadIdx.x; i < n; i += STPB) st[i] = cx<float>(i == 0 ? 1.f : 0.f, 0.f);
+  } else {
+    for (int i = threadIdx.x; i < n; i += STPB) { float2 a = e.state[i]; st[i] = cx<float>(a.x, a.y); }
+  }
+  __syncthreads();
+  for (int k = e.g0; k < e.g1; ++k) {
+    apply_gate_range<float>(st, e.N, e.gates[k], threadIdx.x, STPB);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += STPB) e.state[i] = make_float2(st[i].x, st[i].y);
+  if (!e.final_) return;
+  // results: norm and P(qubit q = 1), FP64, fixed order
+  for (int q = -1; q < e.N; ++q) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += STPB)
+      if (q < 0 || ((i >> q) & 1)) acc += (double)st[i].x * st[i].x + (double)st[i].y * st[i].y;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int w = 0; w < STPB / 32; ++w) r += red[w];
+      e.out[q + 1] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// first-fit allocator over [0, size) with 256-byte granules
+class Pool {
+ public:
+  explicit Pool(size_t size) { free_[0] = size; }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += bytes;
+        peak_ = std::max(peak_, used_);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+    }
+  }
+  size_t peak() const { return peak_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0, peak_ = 0;
+};
+
+struct Active {
+  int id;
+  bool small;
+  size_t off, bytes;          // pool region of the state
+  size_t goff, gbytes;        // pool region of the device gate list (small)
+  int next;                   // next gate
+  bool fresh;
+  qs_sim* sim;                // large: handle over the pool region
+  int stream;
+};
+
+}  // namespace
+
+extern "C" qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* cfg, qs_serve_stats* stats) {
+  if (!reqs || n < 0 || !cfg) { qs_set_error("serve_run: null argument"); return QS_EINVAL; }
+  const int small_max = cfg->small_max_n > 0 ? (cfg->small_max_n < 14 ? cfg->small_max_n : 14) : 14;
+  const int quantum = cfg->quantum > 0 ? cfg->quantum : 64;
+  const int nstreams = cfg->nstreams > 0 ? (cfg->nstreams < 16 ? cfg->nstreams : 16) : 4;
+  const size_t budget = cfg->mem_budget;
+  for (int i = 0; i < n; ++i) {
+    const qs_request& r = reqs[i];
+    if (r.N < 2 || r.N > 34 || r.ngates < 0 || (r.ngates > 0 && !r.gates) || !r.qz) {
+      qs_set_error("serve_run: request %d malformed", i);
+      return QS_EINVAL;
+    }
+    if (((size_t)8 << r.N) + (size_t)r.ngates * sizeof(BGate<float>) + 1024 > budget) {
+      qs_set_error("serve_run: request %d (N = %d) does not fit the memory budget", i, r.N);
+      return QS_ENOMEM;
+    }
+    if (i > 0 && r.arrival_s < reqs[i - 1].arrival_s) { qs_set_error("serve_run: arrivals must be sorted"); return QS_EINVAL; }
+    for (int k = 0; k < r.ngates; ++k) {
+      const qs_gate& g = r.gates[k];
+      if (g.nc < 0 || g.nc > 2 || g.target < 0 || g.target >= r.N) { qs_set_error("serve_run: request %d gate %d", i, k); return QS_EINVAL; }
+      for (int c = 0; c < g.nc; ++c)
+        if (g.controls[c] < 0 || g.controls[c] >= r.N || g.controls[c] == g.target ||
+            (c == 1 && g.controls[1] == g.controls[0])) {
+          qs_set_error("serve_run: request %d gate %d: bad controls", i, k);
+          return QS_EINVAL;
+        }
+      if (!(unitarity_defect(g.u, 2) <= 1e-10)) { qs_set_error("serve_run: request %d gate %d not unitary", i, k); return QS_ENOTUNITARY; }
+    }
+  }
+  // resources
+  unsigned char* pool_base = nullptr;
+  QS_CUDA(cudaMalloc(&pool_base, budget));
+  Pool pool(budget);
+  std::vector<cudaStream_t> streams(nstreams + 1);
+  for (auto& s : streams) QS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  const int max_small = cfg->max_small > 0 ? cfg->max_small : 4096;
+  SmallEntry* htab = nullptr;
+  SmallEntry* dtab = nullptr;
+  double* hres = nullptr;
+  double* dres = nullptr;
+  const size_t res_stride = 40;
+  QS_CUDA(cudaMallocHost(&htab, sizeof(SmallEntry) * max_small));
+  QS_CUDA(cudaMalloc(&dtab, sizeof(SmallEntry) * max_small));
+  QS_CUDA(cudaMallocHost(&hres, sizeof(double) * res_stride * max_small));
+  QS_CUDA(cudaMalloc(&dres, sizeof(double) * res_stride * max_small));
+  QS_CUDA(cudaFuncSetAttribute(k_serve_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14));
+
+  std::vector<Active> active;
+  std::vector<BGate<float>> hg;
+  int next_arrival = 0, completed = 0, ticks = 0, max_active = 0;
+  const uint64_t launches0 = qs_kernel_launches();
+  const auto t0 = std::chrono::steady_clock::now();
+  auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  qs_status st = QS_OK;
+  double busy = 0.0;
+  while (completed < n && st == QS_OK) {
+    // admission: oldest first, while the state and its gate list fit
+    while (next_arrival < n && reqs[next_arrival].arrival_s <= now_s()) {
+      qs_request& r = reqs[next_arrival];
+      Active a;
+      memset(&a, 0, sizeof a);
+      a.id = next_arrival;
+      a.small = r.N <= small_max;
+      a.bytes = (size_t)8 << r.N;
+      a.gbytes = a.small ? (size_t)r.ngates * sizeof(BGate<float>) : 0;
+      if (!pool.alloc(a.bytes, &a.off)) break;
+      if (a.small && a.gbytes && !pool.alloc(a.gbytes, &a.goff)) { pool.release(a.off, a.bytes); break; }
+      a.fresh = true;
+      a.stream = (int)(active.size() % nstreams) + 1;
+      if (a.small && r.ngates) {
+        hg.resize(r.ngates);
+        for (int k = 0; k < r.ngates; ++k) {
+          const qs_gate& g = r.gates[k];
+          BGate<float>& o = hg[k];
+          o.nc = g.nc; o.c0 = g.controls[0]; o.c1 = g.controls[1]; o.t = g.target;
+          for (int j = 0; j < 8; ++j) o.u[j] = (float)g.u[j];
+        }
+        // pageable source: the copy completes before the call returns
+        if (cudaMemcpy(pool_base + a.goff, hg.data(), a.gbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+          qs_set_error("serve_run: gate upload failed");
+          st = QS_ECUDA;
+          break;
+        }
+      }
+      if (!a.small) {
+        st = sim_create_in(r.N, QS_C64, pool_base + a.off, a.bytes, (void*)streams[a.stream], &a.sim);
+        if (st != QS_OK) break;
+      }
+      r.admit_s = now_s();
+      active.push_back(a);
+      ++next_arrival;
+    }
+    if (st != QS_OK) break;
+    max_active = std::max(max_active, (int)active.size());
+    if (active.empty()) {
+      // idle until the next arrival
+      const double wait = reqs[next_arrival].arrival_s - now_s();
+      if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait < 1e-3 ? wait : 1e-3));
+      continue;
+    }
+    const double tick_start = now_s();
+    ++ticks;
+    // small states: one launch for all
+    int ns = 0, maxn = 2;
+    std::vector<int> small_ids;
+    for (auto& a : active) {
+      if (!a.small || ns >= max_small) continue;
+      const qs_request& r = reqs[a.id];
+      SmallEntry& e = htab[ns];
+      e.state = (float2*)(pool_base + a.off);
+      e.gates = (const BGate<float>*)(pool_base + a.goff);
+      e.N = r.N;
+      e.g0 = a.next;
+      e.g1 = std::min(r.ngates, a.next + quantum);
+      e.fresh = a.fresh ? 1 : 0;
+      e.final_ = (e.g1 == r.ngates) ? 1 : 0;
+      e.out = dres + res_stride * ns;
+      maxn = std::max(maxn, r.N);
+      small_ids.push_back((int)(&a - active.data()));
+      ++ns;
+    }
+    if (ns > 0) {
+      QS_CUDA(cudaMemcpyAsync(dtab, htab, sizeof(SmallEntry) * ns, cudaMemcpyHostToDevice, streams[0]));
+      k_serve_small<<<ns, STPB, (size_t)8 << maxn, streams[0]>>>(dtab);
+      qs_count_launch();
+      QS_CUDA(cudaGetLastError());
+      QS_CUDA(cudaMemcpyAsync(hres, dres, sizeof(double) * res_stride * ns, cudaMemcpyDeviceToHost, streams[0]));
+    }
+    // large states: their chunk on their own streams
+    for (auto& a : active) {
+      if (a.small) continue;
+      const qs_request& r = reqs[a.id];
+      const int g1 = std::min(r.ngates, a.next + quantum);
+      if (g1 > a.next) {
+        st = circuit_run(a.sim, r.gates + a.next, g1 - a.next, 1, nullptr);
+        if (st != QS_OK) break;
+      }
+    }
+    if (st != QS_OK) break;
+    for (auto& s : streams) QS_CUDA(cudaStreamSynchronize(s));
+    // bookkeeping and retirement
+    for (int k = 0; k < ns; ++k) {
+      Active& a = active[small_ids[k]];
+      const SmallEntry& e = htab[k];
+      a.fresh = false;
+      a.next = e.g1;
+      if (e.final_) {
+        qs_request& r = reqs[a.id];
+        r.norm = hres[res_stride * k];
+        for (int q = 0; q < r.N; ++q) r.qz[q] = hres[res_stride * k + 1 + q];
+      }
+    }
+    for (auto& a : active) {
+      if (a.small) continue;
+      const qs_request& r = reqs[a.id];
+      a.next = std::min(r.ngates, a.next + quantum);
+    }
+    std::vector<Active> keep;
+    for (auto& a : active) {
+      qs_request& r = reqs[a.id];
+      if (a.next < r.ngates || (a.small && a.fresh)) { keep.push_back(a); continue; }
+      if (!a.small) {
+        std::vector<double> qx(r.N), qy(r.N);
+        st = expect_xyz(a.sim, qx.data(), qy.data(), r.qz);
+        if (st == QS_OK) st = sim_norm(a.sim, &r.norm);
+        sim_destroy(a.sim);
+        if (st != QS_OK) break;
+      }
+      r.finish_s = now_s();
+      pool.release(a.off, a.bytes);
+      if (a.gbytes) pool.release(a.goff, a.gbytes);
+      ++completed;
+    }
+    active.swap(keep);
+    busy += now_s() - tick_start;
+  }
+  const double wall = now_s();
+  for (auto& a : active)
+    if (a.sim) sim_destroy(a.sim);
+  for (auto& s : streams) cudaStreamDestroy(s);
+  cudaFree(pool_base);
+  cudaFree(dtab);
+  cudaFree(dres);
+  cudaFreeHost(htab);
+  cudaFreeHost(hres);
+  if (stats) {
+    stats->completed = completed;
+    stats->ticks = ticks;
+    stats->wall_s = wall;
+    stats->busy_s = busy;
+    stats->launches = qs_kernel_launches() - launches0;
+    stats->peak_bytes = pool.peak();
+    stats->max_active = max_active;
+  }
+  return st;
+}

@@ -42,6 +42,23 @@ class qs_gate(ctypes.Structure):
                 ("target", ctypes.c_int32), ("u", ctypes.c_double * 8)]
 
 
+class qs_request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("N", ctypes.c_int), ("ngates", ctypes.c_int),
+                ("gates", ctypes.POINTER(qs_gate)), ("qz", ctypes.POINTER(ctypes.c_double)),
+                ("norm", ctypes.c_double), ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+
+class qs_serve_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("quantum", ctypes.c_int), ("max_small", ctypes.c_int),
+                ("nstreams", ctypes.c_int), ("small_max_n", ctypes.c_int)]
+
+
+class qs_serve_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int), ("ticks", ctypes.c_int), ("max_active", ctypes.c_int),
+                ("wall_s", ctypes.c_double), ("busy_s", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_size_t)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.POINTER(ctypes.c_double)
@@ -83,6 +100,7 @@ _SIGS = {
     "batch_copy_out": (_I, [_P, _P, ctypes.c_size_t]),
     "batch_copy_in": (_I, [_P, _P, ctypes.c_size_t]),
     "batch_info": (_I, [_P, _IP, _IP, ctypes.POINTER(_P)]),
+    "serve_run": (_I, [ctypes.POINTER(qs_request), _I, ctypes.POINTER(qs_serve_config), ctypes.POINTER(qs_serve_stats)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -398,6 +416,34 @@ class Batch:
         dt = np.complex128 if self.enc == C128 else np.complex64
         a = np.ascontiguousarray(a, dtype=dt)
         _check(_lib.batch_copy_in(self._h, _P(a.ctypes.data), self.nbytes))
+
+
+def serve(requests, mem_budget, quantum=64, nstreams=4, small_max_n=14, max_small=4096):
+    """Run the serving loop.  requests: list of dicts with arrival (s), N and
+    records (gate records).  Returns (results, stats): per request a dict with
+    qz, norm, admit_s, finish_s, latency_s."""
+    n = len(requests)
+    reqs = (qs_request * max(1, n))()
+    keep = []
+    for i, r in enumerate(requests):
+        arr, ng = gate_array(r["records"])
+        qz = np.zeros(r["N"])
+        keep.append((arr, qz))
+        reqs[i].arrival_s = float(r["arrival"])
+        reqs[i].N = int(r["N"])
+        reqs[i].ngates = ng
+        reqs[i].gates = ctypes.cast(arr, ctypes.POINTER(qs_gate))
+        reqs[i].qz = qz.ctypes.data_as(_D)
+    cfg = qs_serve_config(int(mem_budget), int(quantum), int(max_small), int(nstreams), int(small_max_n))
+    st = qs_serve_stats()
+    _check(_lib.serve_run(reqs, n, ctypes.byref(cfg), ctypes.byref(st)))
+    out = []
+    for i in range(n):
+        out.append(dict(qz=keep[i][1].copy(), norm=reqs[i].norm, admit_s=reqs[i].admit_s,
+                        finish_s=reqs[i].finish_s, latency_s=reqs[i].finish_s - reqs[i].arrival_s))
+    stats = dict(completed=st.completed, ticks=st.ticks, max_active=st.max_active, wall_s=st.wall_s,
+                 busy_s=st.busy_s, launches=st.launches, peak_bytes=st.peak_bytes)
+    return out, stats
 
 
 def measure_probs_static(state_ptr, N, enc, qubits, stream=0):
