@@ -41,7 +41,10 @@ METRIC = "gate-amplitude updates/s"
 UNIT = "updates/s"
 # algorithmic bytes of one tile pass: read + write of the whole state
 # (2 * 2^N * 8 B for complex64)
-TILE_TRAFFIC_PER_PASS = None  # dram bytes per tile-pass launch from ncu; None until captured for this kernel
+# DRAM bytes per tile-pass launch at N = 30, from one ncu capture at N = 26
+# scaled by the 16x units (profiles/k_tile2_c64_n26_full.md); set to None when
+# the kernel changes after the capture
+TILE_TRAFFIC_PER_PASS = (543.3e6 + 479.0e6) * 16
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
@@ -183,6 +186,133 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# variants: the other configurations, measured in the same run
+# ---------------------------------------------------------------------------
+def _timed(torch, stream, fn):
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), r
+
+
+def _order(y, G):
+    r, f = 1, y % G
+    while f != 1:
+        f, r = (f * y) % G, r + 1
+    return r
+
+
+def _period(k, X, G):
+    from fractions import Fraction
+    return Fraction(k, 1 << X).limit_denominator(G - 1).denominator if k else None
+
+
+def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N):
+    import numpy as np
+    from paper_1805_04708_gb300 import workloads as wl
+    v = {}
+
+    def per_gate_c64():
+        sim.reset()
+        sim.circuit_run(gates, mode=0)
+    ms, _ = _timed(torch, stream, per_gate_c64)
+    v["c64_per_gate_sweeps"] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
+    sim.close()
+    torch.cuda.empty_cache()
+
+    s128 = qsim.Sim(N, "c128", stream=stream)
+    for mode, key in ((1, "c128_tile_passes"), (0, "c128_per_gate_sweeps")):
+        def run128(mode=mode):
+            s128.reset()
+            s128.circuit_run(gates, mode=mode)
+        run128()
+        ms, _ = _timed(torch, stream, run128)
+        v[key] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
+    s128.close()
+    del s128
+    torch.cuda.empty_cache()
+
+    # Shor period finding, G = 899 = 29 x 31, seeded base, X = 20, F = 10
+    G = 899
+    X, F = (G * G - 1).bit_length(), (G - 1).bit_length()
+    y = wl.coprime_base(G, 1)
+    recs = wl.shor_modmul(G, y, X, F)
+    r = _order(y, G)
+    sh = {"G": G, "y": y, "X": X, "F": F, "gates": len(recs), "order": r}
+    for enc in ("c64", "c128"):
+        s = qsim.Sim(X + F, enc, stream=stream)
+        s.run_records(recs, mode=1)
+        ms, _ = _timed(torch, stream, lambda: (s.reset(), s.run_records(recs, mode=1)))
+        msp, P = _timed(torch, stream, lambda: s.measure_probs(list(range(X - 1, -1, -1))))
+        ks = [int(k) for k in np.argsort(P)[::-1][:8] if k and P[k] > 1e-3]
+        found = sorted({_period(k, X, G) for k in ks} - {None})
+        fac = None
+        if r % 2 == 0:
+            h = pow(y, r // 2, G)
+            fac = sorted({math.gcd(h - 1, G), math.gcd(h + 1, G)} - {1, G}) or None
+        sh[enc] = {"ms": ms + msp, "value": len(recs) * float(1 << (X + F)) / (ms / 1e3),
+                   "periods_from_top_peaks": found, "factors_from_order": fac}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    v["shor_n30_modmul_iqft"] = sh
+
+    # depth-1 layers of the Haar + CNOT-matching family at the full sizes:
+    # adaptive 2-byte N = 36 (128 GiB) and complex128 N = 33 (128 GiB)
+    for enc, NN in (("adapt2", 36), ("c128", 33)):
+        s = qsim.Sim(NN, enc, stream=stream)
+        layer = wl.layered_circuit(NN, 1, seed=3)
+        mode = 0 if enc == "adapt2" else 1
+        ms, _ = _timed(torch, stream, lambda: s.circuit_run(layer, mode=mode))
+        msn, nrm = _timed(torch, stream, lambda: s.norm())
+        v["%s_n%d_layer" % (enc, NN)] = {"gates": len(layer), "ms_per_layer": ms,
+                                         "value": len(layer) * float(1 << NN) / (ms / 1e3),
+                                         "norm_after_layer": nrm, "norm_ms": msn}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+    # serving: a bounded sample of the request stream (Poisson 200/s,
+    # N ~ U{12..28}, depth ~ U{10..100}), continuous batching vs the plain
+    # per-gate path (one request at a time, FIFO)
+    nreq = 48
+    reqs = wl.serving_stream(nreq, 200.0, 7)
+    for rq in reqs:
+        rq["records"] = wl.layered_circuit(rq["N"], rq["depth"], rq["seed"])
+    res, st = qsim.serve(reqs, 48 << 30, quantum=64, nstreams=4)
+    lat = np.array([o["latency_s"] for o in res])
+    upd = sum(len(rq["records"]) * float(1 << rq["N"]) for rq in reqs)
+    serving = {"requests": nreq, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+               "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": st["wall_s"],
+               "circuits_per_s": nreq / st["wall_s"], "updates_per_s": upd / st["wall_s"],
+               "max_active": st["max_active"], "ticks": st["ticks"], "launches": st["launches"],
+               "offered_rate_per_s": 200.0}
+    # per-gate path: each request alone, in arrival order
+    t_free = 0.0
+    lat_pg = []
+    for rq in reqs:
+        s = qsim.Sim(rq["N"], "c64", stream=stream)
+        arr, n = qsim.gate_array(rq["records"])
+        ms, _ = _timed(torch, stream, lambda: s.circuit_run((arr, n), mode=0))
+        s.expect_xyz()
+        s.close()
+        start = max(t_free, rq["arrival"])
+        t_free = start + ms / 1e3
+        lat_pg.append(t_free - rq["arrival"])
+    lat_pg = np.array(lat_pg)
+    serving["per_gate_path"] = {"p50_ms": 1e3 * float(np.percentile(lat_pg, 50)),
+                                "p99_ms": 1e3 * float(np.percentile(lat_pg, 99)),
+                                "circuits_per_s": nreq / t_free}
+    v["serving_stream"] = serving
+    torch.cuda.empty_cache()
+    return v
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -283,33 +413,7 @@ def run_gpu(args):
     # variants measured in the same run (one step each)
     variants = {}
     if not args.no_variants:
-        def timed(fn):
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b)
-
-        def per_gate_c64():
-            sim.reset()
-            sim.circuit_run(gates, mode=0)
-        ms = timed(per_gate_c64)
-        variants["c64_per_gate_sweeps"] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
-        sim.close()
-        del sim
-        torch.cuda.empty_cache()
-        s128 = qsim.Sim(N, "c128", stream=stream)
-        for mode, key in ((1, "c128_tile_passes"), (0, "c128_per_gate_sweeps")):
-            def run128(mode=mode):
-                s128.reset()
-                s128.circuit_run(gates, mode=mode)
-            run128()
-            ms = timed(run128)
-            variants[key] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
-        s128.close()
+        variants = run_variants(qsim, torch, stream, sim, gates, upd_per_step, N)
     else:
         sim.close()
 
