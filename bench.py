@@ -224,6 +224,29 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N):
     sim.close()
     torch.cuda.empty_cache()
 
+    # dense fused k-qubit gates (k = 2..5): tensor cores (k lowest qubits,
+    # 3xTF32 mma.sync) against the CUDA-core kernel (qubits 1..k)
+    s64 = qsim.Sim(N, "c64", stream=stream)
+    fused = {}
+    peak, _ = load_peaks()
+    for k in (2, 3, 4, 5):
+        g = np.random.default_rng(k)
+        Z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
+        Qm, Rm = np.linalg.qr(Z)
+        U = Qm * (np.diag(Rm) / np.abs(np.diag(Rm)))
+        row = {}
+        for qs, key in ((list(range(k)), "tensor_cores"), (list(range(1, k + 1)), "cuda_cores")):
+            s64.apply_fused(qs, U)
+            ms, _ = _timed(torch, stream, lambda: s64.apply_fused(qs, U))
+            gbs = 2.0 * (8 << N) / (ms / 1e3) / 1e9
+            row[key] = {"ms": ms, "GB/s": gbs, "frac_of_hbm_peak": gbs / peak,
+                        "complex_fma_TFLOP/s": 8.0 * (1 << k) * float(1 << N) / (ms / 1e3) / 1e12}
+        fused["k%d" % k] = row
+    v["fused_dense_c64_n30"] = fused
+    s64.close()
+    del s64
+    torch.cuda.empty_cache()
+
     s128 = qsim.Sim(N, "c128", stream=stream)
     for mode, key in ((1, "c128_tile_passes"), (0, "c128_per_gate_sweeps")):
         def run128(mode=mode):

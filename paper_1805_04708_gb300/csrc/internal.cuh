@@ -81,6 +81,9 @@ double unitarity_defect(const double* U, int d);
 qs_status launch_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]);
 // Dense k-qubit gate (C128 / C64).
 qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* U);
+// Dense k-qubit gate on the k lowest qubits of a complex64 state, on tensor
+// cores (qubits: a permutation of 0..k-1, 2 <= k <= 5).
+qs_status launch_fused_tc(qs_sim* s, const int* qubits, int k, const double* U);
 // Register permutation (all encodings).
 qs_status launch_permutation(qs_sim* s, const int* controls, int nc, int reg_lo, int reg_w,
                              const uint32_t* table);

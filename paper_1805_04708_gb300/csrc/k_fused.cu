@@ -55,6 +55,11 @@ __global__ void __launch_bounds__(TPB) k_fused(A* __restrict__ s, FusedGeo g, co
 }  // namespace
 
 qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* U) {
+  if (s->enc == QS_C64 && k >= 2 && s->N >= k + 4) {
+    int mask = 0;
+    for (int m = 0; m < k; ++m) mask |= 1 << qubits[m];
+    if (mask == (1 << k) - 1) return launch_fused_tc(s, qubits, k, U);   // lowest k qubits
+  }
   FusedGeo g;
   g.N = s->N; g.k = k;
   for (int m = 0; m < k; ++m) { g.ins[m] = qubits[m]; g.qpos[m] = qubits[m]; }

@@ -92,6 +92,25 @@ def test_apply_fused_dense(q, enc, k):
     assert np.max(np.abs(got - ref)) <= TOL[enc] * (4 if enc == "c64" and k == 5 else 1)
 
 
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_apply_fused_tensor_cores(q, k):
+    # complex64, gate on the k lowest qubits (any order): the tensor-core path
+    N = 14
+    g = np.random.default_rng(100 + k)
+    v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
+    v0 /= np.linalg.norm(v0)
+    ref = v0.astype(np.complex64).astype(np.complex128)
+    with q.Sim(N, "c64") as s:
+        s.copy_in(v0)
+        for trial in range(3):
+            qubits = [int(x) for x in g.permutation(k)]
+            U = haar(1 << k, 7 * k + trial)
+            s.apply_fused(qubits, U)
+            sv.apply_dense(ref, N, qubits, U)
+        got = s.copy_out()
+    assert np.max(np.abs(got - ref)) <= 1e-5
+
+
 def test_apply_fused_rejects(q):
     with q.Sim(6, "c128") as s:
         with pytest.raises(q.QSError) as e:
