@@ -581,14 +581,25 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
   for (int q = 0; q < 64; ++q) is_target[q] = 0;
   for (int i = 0; i < ng; ++i)
     if (classify_u2(gates[gidx[i]].u).kind != GK_DIAG) is_target[gates[gidx[i]].target] = 1;
+  // Lane qubits: high targets go to the register slots while they fit
+  // (no shuffles); only the targets beyond RB-1 take lanes (best lane score
+  // first), and the remaining lanes take non-target tile qubits.
+  int nhigh_targets = 0;
+  for (int q = LOW_BITS; q < N; ++q)
+    if (((tile >> q) & 1) && is_target[q]) ++nhigh_targets;
+  int lane_targets = nhigh_targets - (RB - 1);
+  if (lane_targets < 0) lane_targets = 0;
   for (int pick = 0; pick < 2; ++pick) {
-    // lane qubits: targets first (so the rest fit the register slots), by score
+    const bool want_target = pick < lane_targets;
     int best = -1;
     for (int q = LOW_BITS; q < N; ++q) {
       if (!((tile >> q) & 1) || local[q] >= 0) continue;
-      if (best < 0 || is_target[q] > is_target[best] || (is_target[q] == is_target[best] && uses[q] < uses[best]))
-        best = q;
+      if (is_target[q] != (want_target ? 1 : 0)) continue;
+      if (best < 0 || uses[q] < uses[best]) best = q;
     }
+    if (best < 0)   // fall back to any tile qubit
+      for (int q = LOW_BITS; q < N && best < 0; ++q)
+        if (((tile >> q) & 1) && local[q] < 0) best = q;
     P->gpos[k] = (uint8_t)best;
     local[best] = k++;
   }
@@ -744,13 +755,18 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
   int ng = 0, launched = 0;
   qs_status st = QS_OK;
   auto flush = [&](uint64_t tile) -> qs_status {
-    // pad the tile to b bits: first with qubits the pass's diagonal gates or
-    // controls use (they become thread-uniform), then the lowest unused bits
-    for (int k = 0; k < ng && __builtin_popcountll(tile) < b; ++k) {
+    // pad the tile to b bits with qubits the pass does not touch at all:
+    // diagonal gates and controls on qubits outside the tile are per-tile
+    // constants (a diagonal folds into one factor), inside it they cost
+    // per-element work
+    uint64_t used = 0;
+    for (int k = 0; k < ng; ++k) {
       const qs_gate& g = gates[gidx[k]];
-      if (classify_u2(g.u).kind == GK_DIAG) tile |= 1ull << g.target;
-      for (int c = 0; c < g.nc && __builtin_popcountll(tile) < b; ++c) tile |= 1ull << g.controls[c];
+      used |= 1ull << g.target;
+      for (int c = 0; c < g.nc; ++c) used |= 1ull << g.controls[c];
     }
+    for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q)
+      if (!((used >> q) & 1)) tile |= 1ull << q;
     for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
     return run_pass(s, gates, gidx, ng, tile, &launched, timer);
   };
