@@ -336,6 +336,22 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N):
 
 
 # ---------------------------------------------------------------------------
+# replicas: whole-job throughput over ranks
+# ---------------------------------------------------------------------------
+def replica_aggregate(elapsed_ms, units, world, device):
+    """Replicas only (no data-path collective): every rank processed `units`
+    in its own `elapsed_ms`; the job time is the slowest rank's, the job
+    throughput is the units of all ranks over that time.  The one collective is
+    this MAX of the timings (NCCL on GPUs, gloo in the CPU tests)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, world * units / (elapsed_ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -396,12 +412,8 @@ def run_gpu(args):
     elapsed_ms = e0.elapsed_time(e1)
     launches = qsim.kernel_launches() - launches0
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms, value = replica_aggregate(elapsed_ms, upd_per_step * args.steps, world, "cuda")
 
-    value = world * upd_per_step * args.steps / (elapsed_ms / 1e3)
     ms_per_step = elapsed_ms / args.steps
 
     # roofline of the dominant kernel: the complex64 tile pass
