@@ -3,7 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-template <typename R> struct Cx { R x, y; };
+template <typename R> struct __align__(2 * sizeof(R)) Cx { R x, y; };
 
 template <typename R>
 __device__ __forceinline__ Cx<R> cx(R x, R y) { Cx<R> c; c.x = x; c.y = y; return c; }
@@ -73,6 +73,26 @@ template <typename R> struct OpAnti {
     Cx<R> b0 = cmul_code(a1, f01, c0);
     Cx<R> b1 = cmul_code(a0, f10, c1);
     a0 = b0; a1 = b1;
+  }
+};
+// Real 2x2 (H, X, CNOT, TOFFOLI, +-Y, ...) on complex64 pairs with packed
+// FP32x2 arithmetic on (re, im): two packed instructions per output.
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define QS_HAVE_F32X2 1
+#endif
+struct OpRealF {
+  float2 u00, u01, u10, u11;   // (u, u) splats
+  __device__ __forceinline__ void pair(Cx<float>& a0, Cx<float>& a1) const {
+    const float2 A0 = make_float2(a0.x, a0.y), A1 = make_float2(a1.x, a1.y);
+#ifdef QS_HAVE_F32X2
+    const float2 B0 = __ffma2_rn(u00, A0, __fmul2_rn(u01, A1));
+    const float2 B1 = __ffma2_rn(u10, A0, __fmul2_rn(u11, A1));
+#else
+    const float2 B0 = make_float2(fmaf(u00.x, A0.x, u01.x * A1.x), fmaf(u00.x, A0.y, u01.x * A1.y));
+    const float2 B1 = make_float2(fmaf(u10.x, A0.x, u11.x * A1.x), fmaf(u10.x, A0.y, u11.x * A1.y));
+#endif
+    a0 = cx<float>(B0.x, B0.y);
+    a1 = cx<float>(B1.x, B1.y);
   }
 };
 template <typename R> struct OpMul {

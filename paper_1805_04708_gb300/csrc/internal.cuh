@@ -60,7 +60,8 @@ enum GateKind : int {
   GK_HAD = 1,     // s * [[1, 1], [1, -1]], s real
   GK_DIAG = 2,    // diag(d0, d1)
   GK_ANTI = 3,    // [[0, f01], [f10, 0]]
-  GK_IDENT = 4    // identity (no-op)
+  GK_IDENT = 4,   // identity (no-op)
+  GK_REAL = 5     // real dense u (tile passes of complex64 states only)
 };
 // Unit factors multiply exactly: 0 = 1, 1 = i, 2 = -1, 3 = -i, 4 = general.
 struct GateClass {

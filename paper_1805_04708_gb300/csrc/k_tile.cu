@@ -181,6 +181,23 @@ __device__ __forceinline__ void lane_op(Cx<R>* v, const TOp& o, int lane, bool t
       }
       return;
     }
+    if (o.kind == GK_REAL) {
+      // real coefficients: packed FP32x2 on (re, im)
+      const float2 cs = hi ? make_float2(o.uf[6], o.uf[6]) : make_float2(o.uf[0], o.uf[0]);
+      const float2 cp = hi ? make_float2(o.uf[4], o.uf[4]) : make_float2(o.uf[2], o.uf[2]);
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const float2 p = make_float2(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (!tok || (j & (int)o.smask) != (int)o.smask) continue;
+#ifdef QS_HAVE_F32X2
+        const float2 r = __ffma2_rn(cs, make_float2(v[j].x, v[j].y), __fmul2_rn(cp, p));
+#else
+        const float2 r = make_float2(fmaf(cs.x, v[j].x, cp.x * p.x), fmaf(cs.x, v[j].y, cp.x * p.y));
+#endif
+        v[j] = cx<R>(r.x, r.y);
+      }
+      return;
+    }
     // each lane keeps cs * own + cp * partner, with per-lane coefficients
     const Cx<R> cs = hi ? u11 : u00, cp = hi ? u10 : u01;
     if (o.smask == 0) {
@@ -264,7 +281,7 @@ __device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t bas
 
 // FEAT: which specialised complex64 paths the pass needs (bit 0: swaps, bit 1:
 // Hadamard-shaped); passes without them run a smaller kernel.
-constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;
+constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_HAD: real-matrix path (packed FP32x2)
 
 // 16-byte global -> shared copies that bypass registers (LDGSTS), so the next
 // tile's loads are in flight while the current tile is computed and stored.
@@ -403,8 +420,10 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
             // of X, Y, CNOT, TOFFOLI)
             // (a register-slot swap as renames makes the register allocation
             // spill at 128 registers; swaps on register slots stay dense)
-            if ((FEAT & FEAT_HAD) && o.kind == GK_HAD) {
-              OpHad<R> f; f.s = uscal<R>(o);
+            if ((FEAT & FEAT_HAD) && o.kind == GK_REAL) {
+              OpRealF f;
+              f.u00 = make_float2(o.uf[0], o.uf[0]); f.u01 = make_float2(o.uf[2], o.uf[2]);
+              f.u10 = make_float2(o.uf[4], o.uf[4]); f.u11 = make_float2(o.uf[6], o.uf[6]);
               reg_op<R, RB>(v, o.a, o.smask, f);
             } else {
               OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
@@ -548,7 +567,7 @@ static int rewrite_pass(const qs_gate* gates, const int* gidx, int ng, qs_gate* 
 // (contains bits 0..5), gidx: the gates in order.  Returns false if the op
 // list overflows (caller splits the pass).
 static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, int N, int b, int RB, uint64_t tile,
-                       TileParams2* P) {
+                       TileParams2* P, bool real_kinds) {
   static thread_local qs_gate seq[MAX_TOPS * 2];
   static thread_local int seq_idx[MAX_TOPS * 2];
   if (ng_in > MAX_TOPS * 2) return false;
@@ -692,6 +711,11 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
       o.type = T_REG;
       o.a = (uint8_t)reg_slot(p);
     }
+    // complex64: real matrices take the packed FP32x2 path, except pure swaps
+    // on lane qubits (those only exchange values)
+    const bool real = (g.u[1] == 0.0 && g.u[3] == 0.0 && g.u[5] == 0.0 && g.u[7] == 0.0);
+    const bool pure_swap = (gc.kind == GK_ANTI && gc.c0 == 0 && gc.c1 == 0);
+    if (real_kinds && real && !diag && (o.type == T_REG || (o.type == T_LANE && !pure_swap))) o.kind = GK_REAL;
     P->ops[nops++] = o;
   }
   // diagonal ops commute: inside each run of them, put the register-slot ones
@@ -805,7 +829,7 @@ static qs_status launch_pass(qs_sim* s, const TileParams2& P, PassTimer* timer) 
     for (int i = 0; i < P.nops; ++i) {
       const TOp& o = P.ops[i];
       if (o.type == T_LANE && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) feat |= FEAT_SWAP;
-      if (o.type == T_REG && o.kind == GK_HAD) feat |= FEAT_HAD;
+      if ((o.type == T_REG || o.type == T_LANE) && o.kind == GK_REAL) feat |= FEAT_HAD;
     }
     const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
     auto go = [&](auto kern) -> qs_status {
@@ -834,7 +858,7 @@ static qs_status run_pass(qs_sim* s, const qs_gate* gates, const int* gidx, int 
                           PassTimer* timer) {
   static thread_local TileParams2 P;
   const int b = tile_bits(s->enc);
-  if (build_pass(gates, gidx, ng, s->N, b, tile_register_bits(s->enc), tile, &P)) {
+  if (build_pass(gates, gidx, ng, s->N, b, tile_register_bits(s->enc), tile, &P, s->enc == QS_C64)) {
     QS_TRY(launch_pass(s, P, timer));
     ++*launched;
     return QS_OK;
