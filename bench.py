@@ -44,7 +44,7 @@ UNIT = "updates/s"
 # DRAM bytes per tile-pass launch at N = 30, from one ncu capture at N = 26
 # scaled by the 16x units (profiles/k_tile2_c64_n26_full.md); set to None when
 # the kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = (543.3e6 + 479.0e6) * 16
+TILE_TRAFFIC_PER_PASS = None
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):

@@ -185,10 +185,11 @@ __device__ __forceinline__ void lane_op(Cx<R>* v, const TOp& o, int lane, bool t
       // real coefficients: packed FP32x2 on (re, im)
       const float2 cs = hi ? make_float2(o.uf[6], o.uf[6]) : make_float2(o.uf[0], o.uf[0]);
       const float2 cp = hi ? make_float2(o.uf[4], o.uf[4]) : make_float2(o.uf[2], o.uf[2]);
+      const bool all = tok && o.smask == 0;
 #pragma unroll
       for (int j = 0; j < (1 << RB); ++j) {
         const float2 p = make_float2(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
-        if (!tok || (j & (int)o.smask) != (int)o.smask) continue;
+        if (!all && (!tok || (j & (int)o.smask) != (int)o.smask)) continue;
 #ifdef QS_HAVE_F32X2
         const float2 r = __ffma2_rn(cs, make_float2(v[j].x, v[j].y), __fmul2_rn(cp, p));
 #else
