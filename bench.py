@@ -224,8 +224,9 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N):
     sim.close()
     torch.cuda.empty_cache()
 
-    # dense fused k-qubit gates (k = 2..5): tensor cores (k lowest qubits,
-    # 3xTF32 mma.sync) against the CUDA-core kernel (qubits 1..k)
+    # dense fused k-qubit gates (k = 2..5) on the k lowest qubits: tcgen05
+    # (k >= 3) and mma.sync tensor-core kernels (3xTF32), against the
+    # CUDA-core kernel (qubits 1..k)
     s64 = qsim.Sim(N, "c64", stream=stream)
     fused = {}
     peak, _ = load_peaks()
@@ -235,7 +236,11 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N):
         Qm, Rm = np.linalg.qr(Z)
         U = Qm * (np.diag(Rm) / np.abs(np.diag(Rm)))
         row = {}
-        for qs, key in ((list(range(k)), "tensor_cores"), (list(range(1, k + 1)), "cuda_cores")):
+        legs = [(list(range(k)), "mma_sync", "mma_sync"), (list(range(1, k + 1)), "cuda_cores", "auto")]
+        if k >= 3:
+            legs.insert(0, (list(range(k)), "tcgen05", "auto"))
+        for qs, key, engine in legs:
+            s64.set_fused_engine(engine)
             s64.apply_fused(qs, U)
             ms, _ = _timed(torch, stream, lambda: s64.apply_fused(qs, U))
             gbs = 2.0 * (8 << N) / (ms / 1e3) / 1e9

@@ -131,6 +131,23 @@ qs_status apply_controlled(qs_sim* sim, const int* controls, int nc, int target,
  * The matrix must be unitary to 1e-10. */
 qs_status apply_fused(qs_sim* sim, const int* qubits, int k, const double* U);
 
+/* Kernel family for apply_fused on QS_C64 states (every choice computes the
+ * same product; the tensor-core paths round each operand as x = hi + lo in
+ * TF32 and keep the three largest partial products, error near FP32
+ * rounding).  The paper has no counterpart: it applies gates one at a time.
+ *  QS_FUSED_AUTO       : tcgen05 tensor cores (TMEM accumulators, bulk-copy
+ *                        streaming) when 3 <= k <= 5, the qubits are
+ *                        0..k-1 in any order and N >= 12; else the mma.sync
+ *                        tensor-core kernel when 2 <= k, the qubits are
+ *                        0..k-1 and N >= k+4; else the CUDA-core kernel.
+ *  QS_FUSED_CUDA_CORES : the CUDA-core kernel for every gate.
+ *  QS_FUSED_MMA_SYNC   : as AUTO without the tcgen05 kernel.
+ * The default is QS_FUSED_AUTO.  Unknown values give QS_EINVAL.  A wait
+ * inside the tcgen05 kernel that runs out (about a second) makes
+ * apply_fused return QS_ETIMEOUT with the state undefined. */
+typedef enum { QS_FUSED_AUTO = 0, QS_FUSED_CUDA_CORES = 1, QS_FUSED_MMA_SYNC = 2 } qs_fused_engine;
+qs_status sim_set_fused_engine(qs_sim* sim, int engine);
+
 /* Controlled register permutation (SHORBOX's f(x) = y^x mod G built from
  * controlled modular multiplications, Sec. 5.4): on every basis index whose
  * nc control bits are all 1, the value f of the register bits

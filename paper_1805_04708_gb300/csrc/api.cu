@@ -57,6 +57,7 @@ static qs_status init_handle(qs_sim* s, int N, qs_encoding enc, void* stream) {
   s->scratch_bytes = 0;
   s->hbuf = nullptr;
   s->hbuf_bytes = 0;
+  s->fused_engine = QS_FUSED_AUTO;
   QS_CUDA(cudaGetDevice(&s->device));
   QS_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
   if (enc == QS_ADAPT2) QS_CUDA(cudaMalloc(&s->a2dev, sizeof(A2Dev)));
@@ -212,6 +213,14 @@ extern "C" qs_status apply_fused(qs_sim* s, const int* qubits, int k, const doub
   }
   if (s->enc == QS_ADAPT2) { qs_set_error("apply_fused: not available for QS_ADAPT2"); return QS_EUNSUPPORTED; }
   return launch_fused_dense(s, qubits, k, U);
+}
+
+extern "C" qs_status sim_set_fused_engine(qs_sim* s, int engine) {
+  QS_TRY(check_sim(s));
+  CHECK_ARG(engine == QS_FUSED_AUTO || engine == QS_FUSED_CUDA_CORES || engine == QS_FUSED_MMA_SYNC,
+            "sim_set_fused_engine: unknown engine %d", engine);
+  s->fused_engine = engine;
+  return QS_OK;
 }
 
 extern "C" qs_status modmul_table(uint64_t a, uint64_t G, int width, uint32_t* table) {

@@ -22,6 +22,7 @@ struct qs_sim {
   size_t hbuf_bytes;
   int device;
   int num_sms;
+  int fused_engine;   // qs_fused_engine for apply_fused on complex64 states
 };
 
 // error reporting ------------------------------------------------------------
@@ -85,6 +86,12 @@ qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* 
 // Dense k-qubit gate on the k lowest qubits of a complex64 state, on tensor
 // cores (qubits: a permutation of 0..k-1, 2 <= k <= 5).
 qs_status launch_fused_tc(qs_sim* s, const int* qubits, int k, const double* U);
+// The same on tcgen05 tensor cores (3 <= k <= 5, N >= 12); eligibility test.
+bool fused_tc05_eligible(const qs_sim* s, const int* qubits, int k);
+qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U);
+// Real block form B (KR x KR, KR = 2^(k+1)) of U^T for the lowest-k-qubit
+// tensor-core kernels.
+void fused_block_matrix(const int* qubits, int k, const double* U, float* B);
 // Register permutation (all encodings).
 qs_status launch_permutation(qs_sim* s, const int* controls, int nc, int reg_lo, int reg_w,
                              const uint32_t* table);

@@ -55,10 +55,12 @@ __global__ void __launch_bounds__(TPB) k_fused(A* __restrict__ s, FusedGeo g, co
 }  // namespace
 
 qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* U) {
-  if (s->enc == QS_C64 && k >= 2 && s->N >= k + 4) {
+  if (s->enc == QS_C64 && s->fused_engine != QS_FUSED_CUDA_CORES) {
+    if (s->fused_engine == QS_FUSED_AUTO && fused_tc05_eligible(s, qubits, k))
+      return launch_fused_tc05(s, qubits, k, U);
     int mask = 0;
     for (int m = 0; m < k; ++m) mask |= 1 << qubits[m];
-    if (mask == (1 << k) - 1) return launch_fused_tc(s, qubits, k, U);   // lowest k qubits
+    if (k >= 2 && s->N >= k + 4 && mask == (1 << k) - 1) return launch_fused_tc(s, qubits, k, U);
   }
   FusedGeo g;
   g.N = s->N; g.k = k;

@@ -111,17 +111,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_fused_tc(float* __restrict__ st,
 }  // namespace
 
 // U: 2^k x 2^k complex, row-major (re, im), local bit m of the index = qubit
-// qubits[m]; qubits is a permutation of 0..k-1.
-qs_status launch_fused_tc(qs_sim* s, const int* qubits, int k, const double* U) {
+// qubits[m]; qubits is a permutation of 0..k-1.  B: KR x KR floats
+// (KR = 2^(k+1)), row-major, the real block form of U^T in natural qubit
+// order (natural index bit m <-> qubit m).
+void fused_block_matrix(const int* qubits, int k, const double* U, float* B) {
   const int K = 1 << k, KR = 2 * K;
-  // natural-order matrix: natural index bit m <-> qubit m
   auto to_api = [&](int nat) {
     int a = 0;
     for (int m = 0; m < k; ++m)
       if ((nat >> qubits[m]) & 1) a |= 1 << m;
     return a;
   };
-  std::vector<float> B((size_t)KR * KR);
   for (int r = 0; r < K; ++r)
     for (int l = 0; l < K; ++l) {
       const int ar = to_api(r), al = to_api(l);
@@ -131,6 +131,12 @@ qs_status launch_fused_tc(qs_sim* s, const int* qubits, int k, const double* U) 
       B[(size_t)(2 * l) * KR + 2 * r + 1] = (float)ui;
       B[(size_t)(2 * l + 1) * KR + 2 * r + 1] = (float)ur;
     }
+}
+
+qs_status launch_fused_tc(qs_sim* s, const int* qubits, int k, const double* U) {
+  const int KR = 2 << k;
+  std::vector<float> B((size_t)KR * KR);
+  fused_block_matrix(qubits, k, U, B.data());
   QS_TRY(ensure_scratch(s, sizeof(float) * B.size()));
   QS_CUDA(cudaMemcpyAsync(s->scratch, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice, s->stream));
   const uint64_t nrows = 1ull << (s->N - k);

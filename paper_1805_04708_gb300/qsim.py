@@ -76,6 +76,7 @@ _SIGS = {
     "apply_gate": (_I, [_P, _I, _D]),
     "apply_controlled": (_I, [_P, _IP, _I, _I, _D]),
     "apply_fused": (_I, [_P, _IP, _I, _D]),
+    "sim_set_fused_engine": (_I, [_P, _I]),
     "apply_permutation": (_I, [_P, _IP, _I, _I, _I, ctypes.POINTER(ctypes.c_uint32)]),
     "modmul_table": (_I, [ctypes.c_uint64, ctypes.c_uint64, _I, ctypes.POINTER(ctypes.c_uint32)]),
     "shorbox_init": (_I, [_P, _I, ctypes.c_uint64, ctypes.c_uint64]),
@@ -243,6 +244,13 @@ class Sim:
         flat[1::2] = U.ravel().imag
         f, fp = _dbl(flat)
         _check(_lib.apply_fused(self._h, q, k, fp))
+
+    FUSED_ENGINES = {"auto": 0, "cuda_cores": 1, "mma_sync": 2}
+
+    def set_fused_engine(self, engine):
+        """Kernel family for apply_fused on complex64 states: "auto" (tcgen05
+        where the gate qualifies), "cuda_cores" or "mma_sync"."""
+        _check(_lib.sim_set_fused_engine(self._h, self.FUSED_ENGINES[engine]))
 
     def apply_permutation(self, controls, reg_lo, reg_w, table):
         c, nc = _ints(controls)

@@ -92,15 +92,19 @@ def test_apply_fused_dense(q, enc, k):
     assert np.max(np.abs(got - ref)) <= TOL[enc] * (4 if enc == "c64" and k == 5 else 1)
 
 
+@pytest.mark.parametrize("N", [12, 14, 21])
 @pytest.mark.parametrize("k", [2, 3, 4, 5])
-def test_apply_fused_tensor_cores(q, k):
-    # complex64, gate on the k lowest qubits (any order): the tensor-core path
-    N = 14
-    g = np.random.default_rng(100 + k)
+@pytest.mark.parametrize("engine", ["auto", "mma_sync"])
+def test_apply_fused_tensor_cores(q, engine, k, N):
+    # complex64, gate on the k lowest qubits (any order): "auto" runs the
+    # tcgen05 kernel for k >= 3 (N >= 12: one CTA at N = 12, several stages
+    # per CTA at N = 21), "mma_sync" the warp-level tensor-core kernel
+    g = np.random.default_rng(100 + k + N)
     v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
     v0 /= np.linalg.norm(v0)
     ref = v0.astype(np.complex64).astype(np.complex128)
     with q.Sim(N, "c64") as s:
+        s.set_fused_engine(engine)
         s.copy_in(v0)
         for trial in range(3):
             qubits = [int(x) for x in g.permutation(k)]
@@ -108,7 +112,35 @@ def test_apply_fused_tensor_cores(q, k):
             s.apply_fused(qubits, U)
             sv.apply_dense(ref, N, qubits, U)
         got = s.copy_out()
+    # 3xTF32 keeps each product near FP32 rounding: after three gates the
+    # deviation is a few FP32 ulps of the unit-norm state
     assert np.max(np.abs(got - ref)) <= 1e-5
+    assert np.linalg.norm(got - ref) <= 2e-6
+
+
+def test_fused_engines_agree(q):
+    # the three kernel families on one k = 5 gate (lowest qubits, N = 16)
+    N, k = 16, 5
+    g = np.random.default_rng(5)
+    v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
+    v0 /= np.linalg.norm(v0)
+    U = haar(1 << k, 99)
+    outs = {}
+    for engine in ("auto", "mma_sync", "cuda_cores"):
+        with q.Sim(N, "c64") as s:
+            s.set_fused_engine(engine)
+            s.copy_in(v0)
+            s.apply_fused(list(range(k)), U)
+            outs[engine] = s.copy_out()
+    for e in ("mma_sync", "cuda_cores"):
+        assert np.linalg.norm(outs["auto"] - outs[e]) <= 1e-6
+    with q.Sim(4, "c64") as s, pytest.raises(KeyError):
+        s.set_fused_engine("tcgen06")
+
+
+def test_fused_engine_rejects_unknown(q):
+    with q.Sim(4, "c64") as s:
+        assert q._lib.sim_set_fused_engine(s._h, 7) == 1     # QS_EINVAL
 
 
 def test_apply_fused_rejects(q):
