@@ -8,37 +8,39 @@
 // form of U^T, each operand split as x = hi + lo in TF32 and
 // D = lo*hi + hi*lo + hi*hi ("3xTF32").
 //
-// Here the state streams through shared memory in stages of 2^12 amplitudes
-// (32 KB, ROWS = 8192 / KR rows), one persistent CTA per SM:
-//  - a bulk copy (cp.async.bulk, completion counted on an mbarrier) brings
-//    stage i+1 into one of two raw buffers while stage i is processed;
-//  - all threads split the raw stage into hi / lo TF32 planes in the
-//    canonical K-major, no-swizzle operand layout: core matrices of 8 rows x
-//    16 bytes, stored 128 bytes apart along the rows (SBO) and 2048 bytes
-//    apart along K (LBO);
-//  - one thread issues 24 tcgen05.mma (kind::tf32, M = 128, N = KR, K = 8):
-//    for each 128-row sub-tile and each K step the products lo*hi, hi*lo,
-//    hi*hi accumulate into columns [s*KR, s*KR + KR) of a 64-column tensor
-//    memory allocation; tcgen05.commit arrives on an mbarrier;
-//  - the warps read the accumulators back (tcgen05.ld 32x32b: lane = row),
-//    write them into the consumed raw buffer (16-byte chunks XOR-swizzled per
-//    row against bank conflicts) and store them, coalesced, where the stage
-//    came from.  Stages are disjoint, so the update is in place.
-// Every wait is bounded: one that runs out makes the CTA wait (again
-// bounded) for the copies and products it has in flight, free its tensor
-// memory and exit, and sets the error word the host reads.
+// One persistent CTA per SM streams "stages" of 2^12 amplitudes (32 KB,
+// 8192 / KR rows) through a ring of NB stage buffers, with warp-specialised
+// roles connected by mbarriers:
+//  - producer (one thread): TMA tensor loads (cp.async.bulk.tensor, 128- or
+//    64-byte swizzle) of boxes of 128 rows x 128 (or 64) bytes, which land
+//    in the canonical K-major swizzled operand layout;
+//  - converters (4 warps): split each element in place into the TF32 hi
+//    part and a second "lo" plane;
+//  - MMA issuer (one thread): per 128-row sub-tile and K step of 8, the
+//    three tcgen05.mma (kind::tf32, M = 128, N = KR) into one of two
+//    64-column accumulators in tensor memory; tcgen05.commit signals the
+//    epilogue;
+//  - epilogue (4 warps, one per TMEM lane quarter): tcgen05.ld of the
+//    accumulators, written back into the stage buffer in the same swizzled
+//    layout, then TMA tensor stores to where the stage came from.
+// Stages are disjoint, so the update is in place.  Every wait is bounded; a
+// wait that runs out raises a CTA-wide abort flag, every role leaves its
+// loop, the producer and the MMA issuer wait (bounded) for what they still
+// have in flight, the tensor memory is freed and the error word is set.
 #include "internal.cuh"
+#include <cuda.h>   // CUtensorMap and its enums; encoded through the runtime's driver entry point
+#include <mutex>
 #include <vector>
 
 namespace {
 
-constexpr int TPB = 256;
-constexpr int STAGE_FLOATS = 8192;             // 2^12 complex64 amplitudes
-constexpr int STAGE_BYTES = STAGE_FLOATS * 4;  // 32 KB
-constexpr int APLANE = STAGE_BYTES;            // one TF32 plane of a stage
-constexpr int LBO_A = 2048;                    // 16 row groups x 128 B
-constexpr int TMEM_COLS = 64;
-constexpr uint32_t WAIT_SPINS = 1u << 20;      // about a second with the back-off below
+constexpr int NWARPS = 10;          // producer, MMA, 4 converters, 4 epilogue
+constexpr int TPB = NWARPS * 32;
+constexpr int STAGE_FLOATS = 8192;  // 2^12 complex64 amplitudes
+constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
+constexpr int NB = 3;               // stage buffers (each a hi and a lo plane)
+constexpr int TMEM_COLS = 128;      // two 64-column accumulators
+constexpr uint32_t WAIT_SPINS = 1u << 20;   // about a second with the back-off below
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -71,12 +73,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
       : "memory");
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
 __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
@@ -96,6 +92,58 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// As mbar_wait, but also gives up when another role has raised the abort
+// flag; raises it itself when the time runs out.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < WAIT_SPINS; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (it >= 64) {
+      if (*abort_flag) return false;
+      __nanosleep(it < 4096 ? 64 : 1024);
+    }
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+// named barrier `id` over n threads, AND-reducing v
+__device__ __forceinline__ bool bar_and(int id, int n, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
@@ -103,11 +151,14 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
-// offsets in 16-byte units, descriptor version 1 (bits 46-47), no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-         (1ull << 46);
+// Shared-memory matrix descriptor of a K-major swizzled operand: start
+// address, stride between 8-row groups (SBO) in 16-byte units, descriptor
+// version 1 (bits 46-47), layout type at bits 61-63 (2 = 128-byte swizzle,
+// 4 = 64-byte swizzle).  The leading offset is unused by swizzled K-major
+// layouts whose K step stays inside one swizzle row; it is set to 1.
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t addr, uint32_t sbo, uint64_t layout) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46) |
+         (layout << 61);
 }
 
 // Instruction descriptor of kind::tf32: F32 accumulator (bits 4-5 = 1), A and
@@ -141,186 +192,213 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
-// Swizzle of the 16-byte chunk j of row r in the staging buffer (V chunks
-// per row): 8 consecutive rows writing the same chunk hit 8 distinct bank
-// groups.
-template <int V>
+
+// Geometry of one stage for KR floats per row.
+template <int KR>
+struct Geo {
+  static constexpr int BOXW = KR >= 32 ? 32 : 16;   // floats per box row
+  static constexpr int ROWB = BOXW * 4;             // bytes per box row = swizzle span
+  static constexpr int BOXB = 128 * ROWB;           // bytes per box (128 rows)
+  static constexpr int QX = KR / BOXW;              // boxes across a row
+  static constexpr int S = 64 / KR;                 // 128-row sub-tiles per stage
+  static constexpr int Q = S * QX;                  // boxes per stage
+  static constexpr int SBO = 8 * ROWB;              // stride of 8-row groups
+  static constexpr uint64_t LAYOUT = KR >= 32 ? 2 : 4;
+  static constexpr int BPLANE = 4 * KR * KR;        // one TF32 plane of B
+  static_assert(Q * BOXB == STAGE_BYTES, "stage = boxes");
+  static_assert(S * KR == 64, "one stage fills one accumulator");
+};
+
+// Swizzled position of the 16-byte chunk j of row r inside a box: the chunk
+// index XOR address bits 7.. (128-byte rows: r mod 8; 64-byte rows:
+// (r / 2) mod 4), as written by the TMA swizzle modes.
+template <int ROWB>
 __device__ __forceinline__ int swz(int r, int j) {
-  return V >= 8 ? (j ^ (r & 7)) : (j ^ ((r >> 1) & 3));
+  return ROWB == 128 ? (j ^ (r & 7)) : (j ^ ((r >> 1) & 3));
 }
 
 template <int KR>
 __global__ void __launch_bounds__(TPB, 1)
-    k_fused_tc05(float* __restrict__ st, uint64_t nstages, const float* __restrict__ Bg, int* __restrict__ err) {
-  constexpr int V = KR / 4;                  // 16-byte chunks per row
-  constexpr int ROWS = STAGE_FLOATS / KR;    // rows per stage
-  constexpr int S = ROWS / 128;              // 128-row sub-tiles per stage
-  constexpr int BPLANE = 4 * KR * KR;        // one TF32 plane of B
-  constexpr int LBO_B = (KR / 8) * 128;      // KR/8 column groups x 128 B
-  constexpr int SUB_A = V * LBO_A;           // bytes of one 128-row sub-tile of A
+    k_fused_tc05(const __grid_constant__ CUtensorMap tmap, uint64_t nstages, const float* __restrict__ Bg,
+                 int* __restrict__ err) {
+  using G = Geo<KR>;
   constexpr uint32_t IDESC = idesc_tf32(KR, 128);
-  static_assert(S * KR == TMEM_COLS, "one stage fills the accumulator columns");
-  static_assert(S * SUB_A == APLANE, "A plane layout");
-
-  extern __shared__ __align__(128) unsigned char smraw[];
-  const uint32_t raw_base = smem_u32(smraw);
-  const uint32_t pad = (128u - (raw_base & 127u)) & 127u;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const uint32_t base0 = smem_u32(smraw);
+  const uint32_t pad = (1024u - (base0 & 1023u)) & 1023u;
   unsigned char* sm = smraw + pad;
-  const uint32_t sb = raw_base + pad;
-  // layout: B hi | B lo | A hi | A lo | raw 0 | raw 1 | 3 mbarriers | tmem slot
-  const uint32_t sBhi = sb, sBlo = sb + BPLANE, sAhi = sb + 2 * BPLANE, sAlo = sAhi + APLANE;
-  const uint32_t sRaw = sAlo + APLANE;
-  const uint32_t sBar = sRaw + 2 * STAGE_BYTES;          // full[0], full[1], mma
-  unsigned char* pBhi = sm;
-  unsigned char* pBlo = sm + BPLANE;
-  unsigned char* pAhi = sm + 2 * BPLANE;
-  unsigned char* pAlo = pAhi + APLANE;
-  unsigned char* pRaw = pAlo + APLANE;
-  uint32_t* tslot = (uint32_t*)(pRaw + 2 * STAGE_BYTES + 24);
+  const uint32_t sb = base0 + pad;
+  // layout: B hi | B lo | NB x (A hi | A lo) | mbarriers | tmem slot, abort flag
+  const uint32_t sBhi = sb, sBlo = sb + G::BPLANE, sA = sb + 2 * G::BPLANE;
+  const uint32_t sBar = sA + NB * 2 * STAGE_BYTES;
+  auto FULL = [&](int b) { return sBar + 8 * b; };
+  auto CONV = [&](int b) { return sBar + 8 * (NB + b); };
+  auto MMAD = [&](int b) { return sBar + 8 * (2 * NB + b); };
+  auto EMPTY = [&](int b) { return sBar + 8 * (3 * NB + b); };
+  auto TFREE = [&](int t) { return sBar + 8 * (4 * NB + t); };
+  uint32_t* tslot = (uint32_t*)(sm + (sBar - sb) + 8 * (4 * NB + 2));
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(sBar, 1);
-    mbar_init(sBar + 8, 1);
-    mbar_init(sBar + 16, 1);
+    for (int b = 0; b < NB; ++b) {
+      mbar_init(FULL(b), 1);
+      mbar_init(CONV(b), 4);
+      mbar_init(MMAD(b), 1);
+      mbar_init(EMPTY(b), 1);
+    }
+    mbar_init(TFREE(0), 4);
+    mbar_init(TFREE(1), 4);
+    *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   // B planes: element (row k, column n) of the KR x KR block matrix is the
-  // K-major operand's (n, k)
+  // K-major operand's (n, k), stored in the swizzled layout of the A boxes
   for (int i = tid; i < KR * KR; i += TPB) {
     const int kk = i / KR, n = i % KR;
     const float x = Bg[i];
     const uint32_t h = to_tf32(x), l = to_tf32(x - __uint_as_float(h));
-    const int off = (kk >> 2) * LBO_B + (n >> 3) * 128 + (n & 7) * 16 + (kk & 3) * 4;
-    *(uint32_t*)(pBhi + off) = h;
-    *(uint32_t*)(pBlo + off) = l;
+    const int hb = kk / G::BOXW, kc = kk % G::BOXW;
+    const int off = hb * (KR * G::ROWB) + n * G::ROWB + swz<G::ROWB>(n, kc >> 2) * 16 + (kc & 3) * 4;
+    *(uint32_t*)(sm + off) = h;
+    *(uint32_t*)(sm + G::BPLANE + off) = l;
   }
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const uint32_t nloc =
+      nstages > blockIdx.x ? (uint32_t)((nstages - 1 - blockIdx.x) / gridDim.x + 1) : 0u;   // stages of this CTA
 
-  const uint64_t first = blockIdx.x, step = gridDim.x;
-  // outstanding work, tracked by thread 0 for the bounded drain after a timeout
-  uint32_t issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0, committed = 0, mma_waited = 0;
-  if (tid == 0 && first < nstages) {
-    mbar_expect_tx(sBar, STAGE_BYTES);
-    bulk_g2s(sRaw, st + first * STAGE_FLOATS, STAGE_BYTES, sBar);
-    issued0 = 1;
-  }
-  bool failed = false;
-  uint32_t it = 0;
-  for (uint64_t g = first; g < nstages; g += step, ++it) {
-    const int b = it & 1;
-    const uint32_t fullb = sBar + 8 * b;
-    unsigned char* praw = pRaw + b * STAGE_BYTES;
-    if (tid == 0 && g + step < nstages) {
-      // the other raw buffer was last read (as staging) before the barrier
-      // that closed the previous iteration
-      fence_async_smem();
-      mbar_expect_tx(sBar + 8 * (b ^ 1), STAGE_BYTES);
-      bulk_g2s(sRaw + (b ^ 1) * STAGE_BYTES, st + (g + step) * STAGE_FLOATS, STAGE_BYTES, sBar + 8 * (b ^ 1));
-      if (b) ++issued0; else ++issued1;
-    }
-    const bool ok_load = mbar_wait(fullb, (it >> 1) & 1);
-    if (__syncthreads_or(!ok_load)) { failed = true; break; }
-    if (tid == 0) { if (b) ++waited1; else ++waited0; }
-
-    // split into TF32 hi / lo planes: a warp covers 8 rows x 4 chunks, the
-    // chunk index rotated by the row so reads and writes spread over the banks
-#pragma unroll 4
-    for (int q = tid; q < ROWS * V; q += TPB) {
-      const int rlo = q & 7, cq = (q >> 3) % V, oct = (q >> 3) / V;
-      const int r = oct * 8 + rlo, c = (cq + rlo) & (V - 1);
-      const float4 x = *(const float4*)(praw + r * (KR * 4) + c * 16);
-      uint4 h, l;
-      h.x = to_tf32(x.x); l.x = to_tf32(x.x - __uint_as_float(h.x));
-      h.y = to_tf32(x.y); l.y = to_tf32(x.y - __uint_as_float(h.y));
-      h.z = to_tf32(x.z); l.z = to_tf32(x.z - __uint_as_float(h.z));
-      h.w = to_tf32(x.w); l.w = to_tf32(x.w - __uint_as_float(h.w));
-      const int rr = r & 127;
-      const int off = (r >> 7) * SUB_A + c * LBO_A + (rr >> 3) * 128 + (rr & 7) * 16;
-      *(uint4*)(pAhi + off) = h;
-      *(uint4*)(pAlo + off) = l;
-    }
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const uint32_t d = tmem + s * KR;
-#pragma unroll
-        for (int ks = 0; ks < KR / 8; ++ks) {
-          const uint32_t ao = s * SUB_A + 2 * ks * LBO_A, bo = 2 * ks * LBO_B;
-          const uint64_t ahi = sdesc(sAhi + ao, LBO_A, 128), alo = sdesc(sAlo + ao, LBO_A, 128);
-          const uint64_t bhi = sdesc(sBhi + bo, LBO_B, 128), blo = sdesc(sBlo + bo, LBO_B, 128);
-          mma_tf32(d, alo, bhi, IDESC, ks > 0);
-          mma_tf32(d, ahi, blo, IDESC, 1);
-          mma_tf32(d, ahi, bhi, IDESC, 1);
-        }
-      }
-      mma_commit(sBar + 16);
-      ++committed;
-    }
-    const bool ok_mma = mbar_wait(sBar + 16, it & 1);
-    if (__syncthreads_or(!ok_mma)) { failed = true; break; }
-    if (tid == 0) ++mma_waited;
-    tc_fence_after();
-
-    // accumulators -> staging (the consumed raw buffer): warp w reads lanes
-    // 32*(w%4).. and column chunks 2*(w/4), 2*(w/4)+1 (16 columns each)
-    {
-      const int q4 = warp & 3, half = warp >> 2;
-      uint32_t v[2][16];
-#pragma unroll
-      for (int jc = 0; jc < 2; ++jc) {
-        const int col0 = 16 * (2 * half + jc);
-        tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + col0, v[jc]);
-      }
-      tmem_wait_ld();
-#pragma unroll
-      for (int jc = 0; jc < 2; ++jc) {
-        const int col0 = 16 * (2 * half + jc);
-        const int s = col0 / KR, cc = col0 % KR;
-        const int r = s * 128 + 32 * q4 + lane;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int j = cc / 4 + t;
-          *(uint4*)(praw + r * (KR * 4) + swz<V>(r, j) * 16) =
-              make_uint4(v[jc][4 * t], v[jc][4 * t + 1], v[jc][4 * t + 2], v[jc][4 * t + 3]);
-        }
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-    float* dst = st + g * STAGE_FLOATS;
-#pragma unroll 4
-    for (int q = tid; q < ROWS * V; q += TPB) {
-      const int r = q / V, j = q % V;
-      *(float4*)(dst + 4 * q) = *(const float4*)(praw + r * (KR * 4) + swz<V>(r, j) * 16);
-    }
-    __syncthreads();
-  }
-
-  if (failed) {
-    if (tid == 0) {
-      atomicExch(err, 1);
-      if (issued0 > waited0) mbar_wait(sBar, (issued0 - 1) & 1);
-      if (issued1 > waited1) mbar_wait(sBar + 8, (issued1 - 1) & 1);
-      if (committed > mma_waited) mbar_wait(sBar + 16, (committed - 1) & 1);
-    }
-    tc_fence_before();
-    __syncthreads();
-  }
   if (warp == 0) {
+    // ---- producer ----
+    if (lane == 0) {
+      uint32_t n_issued = 0;
+      for (uint32_t i = 0; i < nloc; ++i) {
+        const int b = i % NB;
+        if (!mbar_wait_or_abort(EMPTY(b), ((i / NB) & 1) ^ 1, abort_flag)) break;
+        const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
+        const uint32_t hi = sA + b * 2 * STAGE_BYTES;
+        mbar_expect_tx(FULL(b), STAGE_BYTES);
+#pragma unroll
+        for (int q = 0; q < G::Q; ++q)
+          tma_load_3d(hi + q * G::BOXB, &tmap, (q % G::QX) * G::BOXW, 0, (int)(g * G::S + q / G::QX), FULL(b));
+        ++n_issued;
+      }
+      if (*abort_flag)
+        for (uint32_t i = (n_issued > NB ? n_issued - NB : 0); i < n_issued; ++i)
+          mbar_wait(FULL(i % NB), (i / NB) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      uint32_t n_commit = 0;
+      for (uint32_t i = 0; i < nloc; ++i) {
+        const int b = i % NB, t = i & 1;
+        if (!mbar_wait_or_abort(CONV(b), (i / NB) & 1, abort_flag)) break;
+        if (!mbar_wait_or_abort(TFREE(t), ((i >> 1) & 1) ^ 1, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t ahi = sA + b * 2 * STAGE_BYTES, alo = ahi + STAGE_BYTES;
+#pragma unroll
+        for (int s = 0; s < G::S; ++s) {
+          const uint32_t d = tmem + t * 64 + s * KR;
+#pragma unroll
+          for (int ks = 0; ks < KR / 8; ++ks) {
+            const int k0 = 8 * ks, hb = k0 / G::BOXW, wb = (k0 % G::BOXW) * 4;
+            const uint32_t ao = (s * G::QX + hb) * G::BOXB + wb, bo = hb * (KR * G::ROWB) + wb;
+            const uint64_t dah = sdesc_sw(ahi + ao, G::SBO, G::LAYOUT), dal = sdesc_sw(alo + ao, G::SBO, G::LAYOUT);
+            const uint64_t dbh = sdesc_sw(sBhi + bo, G::SBO, G::LAYOUT), dbl = sdesc_sw(sBlo + bo, G::SBO, G::LAYOUT);
+            mma_tf32(d, dal, dbh, IDESC, ks > 0);
+            mma_tf32(d, dah, dbl, IDESC, 1);
+            mma_tf32(d, dah, dbh, IDESC, 1);
+          }
+        }
+        mma_commit(MMAD(b));
+        ++n_commit;
+      }
+      if (*abort_flag && n_commit) mbar_wait(MMAD((n_commit - 1) % NB), ((n_commit - 1) / NB) & 1);
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    // ---- converters: x -> hi (in place) + lo ----
+    const int ct = tid - 64;
+    for (uint32_t i = 0; i < nloc; ++i) {
+      const int b = i % NB;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(FULL(b), (i / NB) & 1, abort_flag));
+      if (!ok) break;
+      unsigned char* hi = sm + (sA - sb) + b * 2 * STAGE_BYTES;
+      unsigned char* lo = hi + STAGE_BYTES;
+#pragma unroll 4
+      for (int q = ct; q < STAGE_BYTES / 16; q += 128) {
+        const float4 x = *(const float4*)(hi + 16 * q);
+        uint4 h, l;
+        h.x = to_tf32(x.x); l.x = to_tf32(x.x - __uint_as_float(h.x));
+        h.y = to_tf32(x.y); l.y = to_tf32(x.y - __uint_as_float(h.y));
+        h.z = to_tf32(x.z); l.z = to_tf32(x.z - __uint_as_float(h.z));
+        h.w = to_tf32(x.w); l.w = to_tf32(x.w - __uint_as_float(h.w));
+        *(uint4*)(hi + 16 * q) = h;
+        *(uint4*)(lo + 16 * q) = l;
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(CONV(b));
+    }
+  } else {
+    // ---- epilogue: accumulators -> stage buffer -> TMA store ----
+    const int q4 = warp & 3;                     // TMEM lane quarter of this warp
+    const bool leader = (warp == 6 && lane == 0);
+    for (uint32_t i = 0; i < nloc; ++i) {
+      const int b = i % NB, t = i & 1;
+      const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NB) & 1, abort_flag));
+      if (!ok) break;
+      tc_fence_after();
+      uint32_t v[4][16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + t * 64 + 16 * c, v[c]);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(TFREE(t));
+      unsigned char* out = sm + (sA - sb) + b * 2 * STAGE_BYTES;   // the hi plane, consumed by the MMA
+      const int r = 32 * q4 + lane;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int s = (16 * c) / KR, c0 = (16 * c) % KR;
+#pragma unroll
+        for (int tq = 0; tq < 4; ++tq) {
+          const int col = c0 + 4 * tq, hb = col / G::BOXW, j = (col % G::BOXW) / 4;
+          *(uint4*)(out + (s * G::QX + hb) * G::BOXB + r * G::ROWB + swz<G::ROWB>(r, j) * 16) =
+              make_uint4(v[c][4 * tq], v[c][4 * tq + 1], v[c][4 * tq + 2], v[c][4 * tq + 3]);
+        }
+      }
+      fence_async_smem();
+      bar_sync(1, 128);
+      if (leader) {
+        const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
+        const uint32_t so = sA + b * 2 * STAGE_BYTES;
+#pragma unroll
+        for (int q = 0; q < G::Q; ++q)
+          tma_store_3d(&tmap, so + q * G::BOXB, (q % G::QX) * G::BOXW, 0, (int)(g * G::S + q / G::QX));
+        bulk_commit();
+        bulk_wait_read0();
+        mbar_arrive(EMPTY(b));
+      }
+    }
+    if (leader) bulk_wait0();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(err, 1);
+  if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -328,7 +406,25 @@ __global__ void __launch_bounds__(TPB, 1)
 
 template <int KR>
 constexpr size_t smem_bytes() {
-  return (size_t)2 * 4 * KR * KR + 4 * (size_t)STAGE_BYTES + 32 + 128;
+  return (size_t)2 * Geo<KR>::BPLANE + (size_t)NB * 2 * STAGE_BYTES + 8 * (4 * NB + 2) + 8 + 1024;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
 }
 
 }  // namespace
@@ -344,6 +440,25 @@ qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U
   const int KR = 2 << k;
   std::vector<float> B((size_t)KR * KR);
   fused_block_matrix(qubits, k, U, B.data());
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    qs_set_error("apply_fused: cuTensorMapEncodeTiled is not available from the driver");
+    return QS_ECUDA;
+  }
+  // the state as a 3-D tensor: KR floats x 128 rows x 2^(N-k-7) blocks
+  const int boxw = KR >= 32 ? 32 : 16;
+  CUtensorMap map;
+  const cuuint64_t dims[3] = {(cuuint64_t)KR, 128, 1ull << (s->N - k - 7)};
+  const cuuint64_t strides[2] = {(cuuint64_t)KR * 4, (cuuint64_t)128 * KR * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)boxw, 128, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->state, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, KR >= 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    qs_set_error("apply_fused: cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return QS_ECUDA;
+  }
   const size_t bbytes = sizeof(float) * B.size();
   QS_TRY(ensure_scratch(s, bbytes + 256));
   int* err = (int*)((char*)s->scratch + bbytes);
@@ -351,11 +466,10 @@ qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U
   QS_CUDA(cudaMemcpyAsync(s->scratch, B.data(), bbytes, cudaMemcpyHostToDevice, s->stream));
   const uint64_t nstages = 1ull << (s->N - 12);
   const unsigned grid = (unsigned)(nstages < (uint64_t)s->num_sms ? nstages : (uint64_t)s->num_sms);
-  float* st = (float*)s->state;
   const float* Bd = (const float*)s->scratch;
   auto go = [&](auto kern, size_t smem) -> qs_status {
     QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, TPB, smem, s->stream>>>(st, nstages, Bd, err);
+    kern<<<grid, TPB, smem, s->stream>>>(map, nstages, Bd, err);
     return QS_OK;
   };
   switch (k) {
