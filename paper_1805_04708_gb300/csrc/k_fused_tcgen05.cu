@@ -9,20 +9,22 @@
 // D = lo*hi + hi*lo + hi*hi ("3xTF32").
 //
 // One persistent CTA per SM streams "stages" of 2^12 amplitudes (32 KB,
-// 8192 / KR rows) through a ring of NB stage buffers, with warp-specialised
-// roles connected by mbarriers:
+// 8192 / KR rows) through a ring of NBH stage buffers (plus a ring of NBL
+// planes for the lo parts), with warp-specialised roles connected by
+// mbarriers:
 //  - producer (one thread): TMA tensor loads (cp.async.bulk.tensor, 128- or
 //    64-byte swizzle) of boxes of 128 rows x 128 (or 64) bytes, which land
 //    in the canonical K-major swizzled operand layout;
-//  - converters (4 warps): split each element in place into the TF32 hi
-//    part and a second "lo" plane;
+//  - converters (4 warps): split each element into the TF32 hi part (in
+//    place) and the lo part (into a lo plane);
 //  - MMA issuer (one thread): per 128-row sub-tile and K step of 8, the
 //    three tcgen05.mma (kind::tf32, M = 128, N = KR) into one of two
 //    64-column accumulators in tensor memory; tcgen05.commit signals the
 //    epilogue;
 //  - epilogue (4 warps, one per TMEM lane quarter): tcgen05.ld of the
 //    accumulators, written back into the stage buffer in the same swizzled
-//    layout, then TMA tensor stores to where the stage came from.
+//    layout, then TMA tensor stores to where the stage came from; the
+//    buffer goes back to the producer once the store has read it.
 // Stages are disjoint, so the update is in place.  Every wait is bounded; a
 // wait that runs out raises a CTA-wide abort flag, every role leaves its
 // loop, the producer and the MMA issuer wait (bounded) for what they still
@@ -38,9 +40,10 @@ constexpr int NWARPS = 10;          // producer, MMA, 4 converters, 4 epilogue
 constexpr int TPB = NWARPS * 32;
 constexpr int STAGE_FLOATS = 8192;  // 2^12 complex64 amplitudes
 constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
-constexpr int NB = 3;               // stage buffers (each a hi and a lo plane)
+constexpr int NBH = 4;              // stage buffers (data, then hi part, then result)
+constexpr int NBL = 2;              // lo planes
 constexpr int TMEM_COLS = 128;      // two 64-column accumulators
-constexpr uint32_t WAIT_SPINS = 1u << 20;   // about a second with the back-off below
+constexpr uint32_t WAIT_SPINS = 1u << 20;   // suspensions of at most ~1 us each
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -73,22 +76,23 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
       : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+// One potentially blocking test: the thread is suspended in hardware until
+// the phase of parity `parity` completes or about `hint_ns` pass.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
       : "memory");
   return done != 0;
 }
 
-// Wait for the phase of parity `parity` to complete; false after ~1 s.
+// Wait for the phase of parity `parity` to complete; false after about a
+// second (WAIT_SPINS suspensions of at most a microsecond).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < WAIT_SPINS; ++it) {
-    if (mbar_test(bar, parity)) return true;
-    if (it >= 64) __nanosleep(it < 4096 ? 64 : 1024);
-  }
+  for (uint32_t it = 0; it < WAIT_SPINS; ++it)
+    if (mbar_try(bar, parity, 1000)) return true;
   return false;
 }
 
@@ -96,11 +100,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // flag; raises it itself when the time runs out.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   for (uint32_t it = 0; it < WAIT_SPINS; ++it) {
-    if (mbar_test(bar, parity)) return true;
-    if (it >= 64) {
-      if (*abort_flag) return false;
-      __nanosleep(it < 4096 ? 64 : 1024);
-    }
+    if (mbar_try(bar, parity, 1000)) return true;
+    if (*abort_flag) return false;
   }
   *abort_flag = 1;
   return false;
@@ -228,24 +229,30 @@ __global__ void __launch_bounds__(TPB, 1)
   const uint32_t pad = (1024u - (base0 & 1023u)) & 1023u;
   unsigned char* sm = smraw + pad;
   const uint32_t sb = base0 + pad;
-  // layout: B hi | B lo | NB x (A hi | A lo) | mbarriers | tmem slot, abort flag
+  // layout: B hi | B lo | NBH stage buffers | NBL lo planes | mbarriers |
+  // tmem slot, abort flag
   const uint32_t sBhi = sb, sBlo = sb + G::BPLANE, sA = sb + 2 * G::BPLANE;
-  const uint32_t sBar = sA + NB * 2 * STAGE_BYTES;
-  auto FULL = [&](int b) { return sBar + 8 * b; };
-  auto CONV = [&](int b) { return sBar + 8 * (NB + b); };
-  auto MMAD = [&](int b) { return sBar + 8 * (2 * NB + b); };
-  auto EMPTY = [&](int b) { return sBar + 8 * (3 * NB + b); };
-  auto TFREE = [&](int t) { return sBar + 8 * (4 * NB + t); };
-  uint32_t* tslot = (uint32_t*)(sm + (sBar - sb) + 8 * (4 * NB + 2));
+  const uint32_t sLo = sA + NBH * STAGE_BYTES;
+  const uint32_t sBar = sLo + NBL * STAGE_BYTES;
+  auto FULL = [&](int b) { return sBar + 8 * b; };                  // stage landed
+  auto EMPTY = [&](int b) { return sBar + 8 * (NBH + b); };         // buffer free
+  auto MMAD = [&](int b) { return sBar + 8 * (2 * NBH + b); };      // products done
+  auto CONV = [&](int l) { return sBar + 8 * (3 * NBH + l); };      // split done
+  auto LOFREE = [&](int l) { return sBar + 8 * (3 * NBH + NBL + l); };   // lo plane read
+  auto TFREE = [&](int t) { return sBar + 8 * (3 * NBH + 2 * NBL + t); };  // accumulator read
+  uint32_t* tslot = (uint32_t*)(sm + (sBar - sb) + 8 * (3 * NBH + 2 * NBL + 2));
   volatile int* abort_flag = (volatile int*)(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int b = 0; b < NB; ++b) {
+    for (int b = 0; b < NBH; ++b) {
       mbar_init(FULL(b), 1);
-      mbar_init(CONV(b), 4);
-      mbar_init(MMAD(b), 1);
       mbar_init(EMPTY(b), 1);
+      mbar_init(MMAD(b), 1);
+    }
+    for (int l = 0; l < NBL; ++l) {
+      mbar_init(CONV(l), 4);
+      mbar_init(LOFREE(l), 1);
     }
     mbar_init(TFREE(0), 4);
     mbar_init(TFREE(1), 4);
@@ -282,10 +289,10 @@ __global__ void __launch_bounds__(TPB, 1)
     if (lane == 0) {
       uint32_t n_issued = 0;
       for (uint32_t i = 0; i < nloc; ++i) {
-        const int b = i % NB;
-        if (!mbar_wait_or_abort(EMPTY(b), ((i / NB) & 1) ^ 1, abort_flag)) break;
+        const int b = i % NBH;
+        if (!mbar_wait_or_abort(EMPTY(b), ((i / NBH) & 1) ^ 1, abort_flag)) break;
         const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
-        const uint32_t hi = sA + b * 2 * STAGE_BYTES;
+        const uint32_t hi = sA + b * STAGE_BYTES;
         mbar_expect_tx(FULL(b), STAGE_BYTES);
 #pragma unroll
         for (int q = 0; q < G::Q; ++q)
@@ -293,8 +300,8 @@ __global__ void __launch_bounds__(TPB, 1)
         ++n_issued;
       }
       if (*abort_flag)
-        for (uint32_t i = (n_issued > NB ? n_issued - NB : 0); i < n_issued; ++i)
-          mbar_wait(FULL(i % NB), (i / NB) & 1);
+        for (uint32_t i = (n_issued > NBH ? n_issued - NBH : 0); i < n_issued; ++i)
+          mbar_wait(FULL(i % NBH), (i / NBH) & 1);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -302,11 +309,11 @@ __global__ void __launch_bounds__(TPB, 1)
     if (lane == 0) {
       uint32_t n_commit = 0;
       for (uint32_t i = 0; i < nloc; ++i) {
-        const int b = i % NB, t = i & 1;
-        if (!mbar_wait_or_abort(CONV(b), (i / NB) & 1, abort_flag)) break;
+        const int b = i % NBH, l = i % NBL, t = i & 1;
+        if (!mbar_wait_or_abort(CONV(l), (i / NBL) & 1, abort_flag)) break;
         if (!mbar_wait_or_abort(TFREE(t), ((i >> 1) & 1) ^ 1, abort_flag)) break;
         tc_fence_after();
-        const uint32_t ahi = sA + b * 2 * STAGE_BYTES, alo = ahi + STAGE_BYTES;
+        const uint32_t ahi = sA + b * STAGE_BYTES, alo = sLo + l * STAGE_BYTES;
 #pragma unroll
         for (int s = 0; s < G::S; ++s) {
           const uint32_t d = tmem + t * 64 + s * KR;
@@ -322,20 +329,22 @@ __global__ void __launch_bounds__(TPB, 1)
           }
         }
         mma_commit(MMAD(b));
+        mma_commit(LOFREE(l));
         ++n_commit;
       }
-      if (*abort_flag && n_commit) mbar_wait(MMAD((n_commit - 1) % NB), ((n_commit - 1) / NB) & 1);
+      if (*abort_flag && n_commit) mbar_wait(MMAD((n_commit - 1) % NBH), ((n_commit - 1) / NBH) & 1);
     }
     __syncwarp();
   } else if (warp < 6) {
     // ---- converters: x -> hi (in place) + lo ----
     const int ct = tid - 64;
     for (uint32_t i = 0; i < nloc; ++i) {
-      const int b = i % NB;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait_or_abort(FULL(b), (i / NB) & 1, abort_flag));
-      if (!ok) break;
-      unsigned char* hi = sm + (sA - sb) + b * 2 * STAGE_BYTES;
-      unsigned char* lo = hi + STAGE_BYTES;
+      const int b = i % NBH, l = i % NBL;
+      bool ok = mbar_wait_or_abort(FULL(b), (i / NBH) & 1, abort_flag);
+      ok = ok && mbar_wait_or_abort(LOFREE(l), ((i / NBL) & 1) ^ 1, abort_flag);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      unsigned char* hi = sm + (sA - sb) + b * STAGE_BYTES;
+      unsigned char* lo = sm + (sLo - sb) + l * STAGE_BYTES;
 #pragma unroll 4
       for (int q = ct; q < STAGE_BYTES / 16; q += 128) {
         const float4 x = *(const float4*)(hi + 16 * q);
@@ -349,15 +358,15 @@ __global__ void __launch_bounds__(TPB, 1)
       }
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(CONV(b));
+      if (lane == 0) mbar_arrive(CONV(l));
     }
   } else {
     // ---- epilogue: accumulators -> stage buffer -> TMA store ----
     const int q4 = warp & 3;                     // TMEM lane quarter of this warp
     const bool leader = (warp == 6 && lane == 0);
     for (uint32_t i = 0; i < nloc; ++i) {
-      const int b = i % NB, t = i & 1;
-      const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NB) & 1, abort_flag));
+      const int b = i % NBH, t = i & 1;
+      const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NBH) & 1, abort_flag));
       if (!ok) break;
       tc_fence_after();
       uint32_t v[4][16];
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(TPB, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(TFREE(t));
-      unsigned char* out = sm + (sA - sb) + b * 2 * STAGE_BYTES;   // the hi plane, consumed by the MMA
+      unsigned char* out = sm + (sA - sb) + b * STAGE_BYTES;   // the hi part, consumed by the MMA
       const int r = 32 * q4 + lane;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -383,7 +392,7 @@ __global__ void __launch_bounds__(TPB, 1)
       bar_sync(1, 128);
       if (leader) {
         const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
-        const uint32_t so = sA + b * 2 * STAGE_BYTES;
+        const uint32_t so = sA + b * STAGE_BYTES;
 #pragma unroll
         for (int q = 0; q < G::Q; ++q)
           tma_store_3d(&tmap, so + q * G::BOXB, (q % G::QX) * G::BOXW, 0, (int)(g * G::S + q / G::QX));
@@ -406,7 +415,7 @@ __global__ void __launch_bounds__(TPB, 1)
 
 template <int KR>
 constexpr size_t smem_bytes() {
-  return (size_t)2 * Geo<KR>::BPLANE + (size_t)NB * 2 * STAGE_BYTES + 8 * (4 * NB + 2) + 8 + 1024;
+  return (size_t)2 * Geo<KR>::BPLANE + (size_t)(NBH + NBL) * STAGE_BYTES + 8 * (3 * NBH + 2 * NBL + 2) + 8 + 1024;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
