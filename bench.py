@@ -427,7 +427,7 @@ def run_gpu(args):
     mean_pass = sum(pass_ms) / len(pass_ms)
     achieved = alg_bytes / (mean_pass / 1e3) / 1e9
     passes_per_step = len(pass_ms) // args.steps
-    roofline = {"kernel": "k_tile<float,float2> (complex64 tile pass)", "bound": "hbm",
+    roofline = {"kernel": "k_tile2 (complex64 tile pass)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "traffic": TILE_TRAFFIC_PER_PASS, "algorithmic_bytes_per_launch": alg_bytes,
@@ -474,6 +474,51 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small fixed workload for profilers (no timing, no JSON line): the
+    state must exceed the 129 MB L2 for DRAM counters to mean something, and
+    stay a few GB so that a multi-pass capture ends quickly.
+      tile   : the random-gate circuit (N qubits, 200 gates, seed 1) through
+               the tile passes twice, then <Qx,Qy,Qz> (complex64)
+      fused  : a dense k-qubit gate on qubits 0..k-1, applied three times
+               (complex64; the tcgen05 kernel for k >= 3)
+      ops    : four single-pass circuits of one op class each (complex64):
+               an empty pass, 20 H on register-slot qubits, 21 H on lane
+               qubits, 20 U3 on register-slot qubits"""
+    import numpy as np
+    import torch
+    from paper_1805_04708_gb300 import qsim
+    from paper_1805_04708_gb300 import workloads as wl
+    N = args.qubits
+    with qsim.Sim(N, "c64") as s:
+        if args.profile_case == "ops":
+            top = N - 1
+            slots = [0, top - 6, top - 5, top - 4, top - 3]      # register slots
+            lanes = [1, 2, 3]                                    # lane qubits
+            for recs in ([("T", (top,), ())],
+                         [("H", (q,), ()) for q in slots] * 4,
+                         [("H", (q,), ()) for q in lanes] * 7,
+                         [("U3", (q,), (0.3, 0.5, 0.7)) for q in slots] * 4):
+                s.circuit_run(recs, mode=1)
+        elif args.profile_case == "tile":
+            recs = wl.random_gate_circuit(N, N_GATES, SEED)
+            for _ in range(2):
+                s.reset()
+                s.circuit_run(recs, mode=1)
+            s.expect_xyz()
+        else:
+            k = args.k
+            g = np.random.default_rng(k)
+            Z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
+            Qm, Rm = np.linalg.qr(Z)
+            U = Qm * (np.diag(Rm) / np.abs(np.diag(Rm)))
+            for _ in range(3):
+                s.apply_fused(list(range(k)), U)
+        print("profile case %s N=%d norm %.12f" % (args.profile_case, N, s.norm()))
+    torch.cuda.synchronize()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,7 +527,13 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", choices=["tile", "fused", "ops"], default=None,
+                    help="run a small workload for a profiler and exit")
+    ap.add_argument("--qubits", type=int, default=26)
+    ap.add_argument("--k", type=int, default=5)
     args = ap.parse_args(argv)
+    if args.profile_case:
+        return run_profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

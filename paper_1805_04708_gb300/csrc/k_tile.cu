@@ -761,56 +761,77 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
 int tile_register_bits(qs_encoding enc) { return enc == QS_C128 ? 4 : 5; }
 int tile_bits(qs_encoding enc) { return tile_register_bits(enc) + LANE_BITS + WARP_BITS; }
 
-// Greedy: extend the current pass while the union of the non-diagonal
-// targets fits in the tile; a pass whose op list overflows is split.
+// Pass packing.  Each pass takes gates in circuit order while the union of
+// their non-diagonal targets fits the tile; a gate that does not fit is left
+// for a later pass, and so is every later gate that does not commute with a
+// gate left out.  Two gates commute when every qubit they share is one on
+// which both act diagonally (a control, or the target of a diagonal gate):
+// both are then block-diagonal on the shared qubits and act on disjoint
+// qubits inside each block.  Every gate a pass takes therefore commutes with
+// all the earlier gates it overtakes, and the product equals the circuit's.
+// A pass whose op list overflows is split.
 static qs_status run_pass(qs_sim* s, const qs_gate* gates, const int* gidx, int ng, uint64_t tile, int* launched,
                           PassTimer* timer);
 
 qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer) {
   const int b = tile_bits(s->enc);
   const int N = s->N;
+  // per gate: qubits acted on non-diagonally (X) and diagonally (Z)
   int* gidx = (int*)malloc(sizeof(int) * (size_t)(n + 1));
-  if (!gidx) return QS_ENOMEM;
+  int* rem = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+  uint64_t* xq = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n + 1));
+  uint64_t* zq = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(n + 1));
+  if (!gidx || !rem || !xq || !zq) {
+    free(gidx); free(rem); free(xq); free(zq);
+    return QS_ENOMEM;
+  }
+  int nrem = 0;
+  for (int i = 0; i < n; ++i) {
+    GateClass gc = classify_u2(gates[i].u);
+    if (gc.kind == GK_IDENT) continue;
+    uint64_t z = 0;
+    for (int c = 0; c < gates[i].nc; ++c) z |= 1ull << gates[i].controls[c];
+    if (gc.kind == GK_DIAG) { xq[i] = 0; z |= 1ull << gates[i].target; }
+    else xq[i] = 1ull << gates[i].target;
+    zq[i] = z;
+    rem[nrem++] = i;
+  }
   const uint64_t low = (1ull << LOW_BITS) - 1;
   // A transpose costs about a third of a sweep, so a pass takes only as many
   // high targets as the lanes and register slots hold (no transposes); the
   // warp bits are padding.
   const int max_targets = LOW_BITS + 2 + (tile_register_bits(s->enc) - 1);
-  uint64_t S = low;
-  int ng = 0, launched = 0;
+  int launched = 0;
   qs_status st = QS_OK;
-  auto flush = [&](uint64_t tile) -> qs_status {
+  while (nrem > 0 && st == QS_OK) {
+    uint64_t S = low, bx = 0, bz = 0;
+    int ng = 0, nleft = 0;
+    for (int k = 0; k < nrem; ++k) {
+      const int i = rem[k];
+      const bool blocked = (xq[i] & (bx | bz)) != 0 || ((xq[i] | zq[i]) & bx) != 0;
+      if (!blocked && __builtin_popcountll(S | xq[i]) <= max_targets && ng < MAX_TOPS / 2) {
+        S |= xq[i];
+        gidx[ng++] = i;
+      } else {
+        bx |= xq[i];
+        bz |= zq[i];
+        rem[nleft++] = i;
+      }
+    }
+    nrem = nleft;
     // pad the tile to b bits with qubits the pass does not touch at all:
     // diagonal gates and controls on qubits outside the tile are per-tile
     // constants (a diagonal folds into one factor), inside it they cost
     // per-element work
     uint64_t used = 0;
-    for (int k = 0; k < ng; ++k) {
-      const qs_gate& g = gates[gidx[k]];
-      used |= 1ull << g.target;
-      for (int c = 0; c < g.nc; ++c) used |= 1ull << g.controls[c];
-    }
+    for (int k = 0; k < ng; ++k) used |= xq[gidx[k]] | zq[gidx[k]];
+    uint64_t tile = S;
     for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q)
       if (!((used >> q) & 1)) tile |= 1ull << q;
     for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
-    return run_pass(s, gates, gidx, ng, tile, &launched, timer);
-  };
-  for (int i = 0; i < n && st == QS_OK; ++i) {
-    GateClass gc = classify_u2(gates[i].u);
-    if (gc.kind == GK_IDENT) continue;
-    uint64_t need = (gc.kind == GK_DIAG) ? 0ull : (1ull << gates[i].target);
-    uint64_t S2 = S | need;
-    if ((__builtin_popcountll(S2) > max_targets || ng >= MAX_TOPS / 2) && ng > 0) {
-      st = flush(S);
-      ng = 0;
-      S = low | need;
-    } else {
-      S = S2;
-    }
-    gidx[ng++] = i;
+    st = run_pass(s, gates, gidx, ng, tile, &launched, timer);
   }
-  if (st == QS_OK && ng > 0) st = flush(S);
-  free(gidx);
+  free(gidx); free(rem); free(xq); free(zq);
   if (n_passes) *n_passes = launched;
   return st;
 }

@@ -42,10 +42,12 @@ def maxerr(a, b):
 
 
 @pytest.mark.parametrize("enc", ["c128", "c64"])
-@pytest.mark.parametrize("N", [2, 3, 5, 8, 11])
+@pytest.mark.parametrize("N", [2, 3, 5, 8, 11, 14, 17])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_random_mixed_circuit(q, enc, N, mode):
-    recs = wl.random_mixed_circuit(N, 50, seed=100 + N)
+    # N >= 14 exceeds one tile: several passes, with commuting gates moved
+    # ahead of the gates left for later passes
+    recs = wl.random_mixed_circuit(N, 50 if N < 14 else 160, seed=100 + N)
     v0 = rand_state(N, N)
     ref = circuit.run(stored(v0, enc).copy(), N, recs)
     with q.Sim(N, enc) as s:
@@ -53,6 +55,25 @@ def test_random_mixed_circuit(q, enc, N, mode):
         s.circuit_run(recs, mode=mode)
         got = s.copy_out()
     assert maxerr(got, ref) <= TOL[enc]
+
+
+@pytest.mark.parametrize("enc", ["c128", "c64"])
+@pytest.mark.parametrize("N", [16, 21])
+def test_tile_pass_packing(q, enc, N):
+    # H / T / RZ / CNOT / TOFFOLI on random qubits: most gates commute with
+    # some of their neighbours, so the passes take gates out of circuit order;
+    # the state must equal the per-gate sweeps' and the oracle's
+    recs = wl.random_gate_circuit(N, 300, seed=40 + N)
+    ref = circuit.run(sv.zero_state(N), N, recs)
+    with q.Sim(N, enc) as s:
+        npass = s.circuit_run(recs, mode=1)
+        got = s.copy_out()
+    with q.Sim(N, enc) as s:
+        s.circuit_run(recs, mode=0)
+        per_gate = s.copy_out()
+    assert maxerr(got, ref) <= TOL[enc]
+    assert maxerr(got, per_gate) <= TOL[enc]
+    assert 1 < npass < len(recs) // 4
 
 
 @pytest.mark.parametrize("enc", ["c128", "c64"])
