@@ -52,6 +52,11 @@ def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
     return wl.random_gate_circuit(N, ngates, seed)
 
 
+TILE_MODES = {1: "op interpreter k_tile2",
+              2: "kernels compiled per pass structure for passes of <= 16 ops, interpreter for the rest",
+              3: "kernels compiled per pass structure"}
+
+
 def config_dict(N, enc):
     return {
         "workload": "random-gate circuit N=%d: %d H + %d gates from {H,T,RZ,CNOT,TOFFOLI}, seed %d, "
@@ -59,7 +64,6 @@ def config_dict(N, enc):
         "N": N, "encoding": enc, "gates_per_step": N + N_GATES,
         "state_bytes": (8 if enc == "c64" else 16) << N,
         "l2": "inputs larger than L2 (no flush)",
-        "path": "tile-pass planner (circuit_run mode 1)",
     }
 
 
@@ -211,10 +215,24 @@ def _period(k, X, G):
     return Fraction(k, 1 << X).limit_denominator(G - 1).denominator if k else None
 
 
-def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N):
+def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
     import numpy as np
     from paper_1805_04708_gb300 import workloads as wl
     v = {}
+
+    def tile_mode(m):
+        def run():
+            sim.reset()
+            sim.circuit_run(gates, mode=m)
+        run()
+        ms, _ = _timed(torch, stream, run)
+        return {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
+    for m in (1, 2, 3):
+        if m != 1 and not qsim.tile_compiler_info()[0]:
+            continue
+        if m != 1:
+            qsim.circuit_compile(N, gates, mode=m)
+        v["c64_tile_mode%d" % m] = dict(tile_mode(m), kernels=TILE_MODES[m])
 
     def per_gate_c64():
         sim.reset()
@@ -384,10 +402,19 @@ def run_gpu(args):
     upd_per_step = ngates * float(1 << N)
     stream = torch.cuda.current_stream()
     sim = qsim.Sim(N, "c64", stream=stream)
+    # tile-pass kernels: compiled per pass structure where that is faster
+    # (mode 2; compiled once here, before any timing), else the interpreter
+    mode = args.tile_mode
+    if mode == 0:
+        mode = 2 if qsim.tile_compiler_info()[0] else 1
+    t_compile = time.perf_counter()
+    if mode in (2, 3):
+        qsim.circuit_compile(N, gates, mode=mode)
+    t_compile = time.perf_counter() - t_compile
 
     def step(timed_passes=None):
         sim.reset()
-        ms = sim.circuit_run_timed(gates, mode=1)
+        ms = sim.circuit_run_timed(gates, mode=mode)
         if timed_passes is not None:
             timed_passes.extend(ms)
         sim.norm()
@@ -427,7 +454,7 @@ def run_gpu(args):
     mean_pass = sum(pass_ms) / len(pass_ms)
     achieved = alg_bytes / (mean_pass / 1e3) / 1e9
     passes_per_step = len(pass_ms) // args.steps
-    roofline = {"kernel": "k_tile2 (complex64 tile pass)", "bound": "hbm",
+    roofline = {"kernel": "complex64 tile pass (%s)" % TILE_MODES[mode], "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "traffic": TILE_TRAFFIC_PER_PASS, "algorithmic_bytes_per_launch": alg_bytes,
@@ -441,7 +468,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sim.reset()
-        sim.circuit_run(recs, mode=1)
+        sim.circuit_run(recs, mode=mode)
         sim.norm()
         sim.expect_xyz()
     torch.cuda.synchronize()
@@ -453,7 +480,7 @@ def run_gpu(args):
     # variants measured in the same run (one step each)
     variants = {}
     if not args.no_variants:
-        variants = run_variants(qsim, torch, stream, sim, gates, upd_per_step, N)
+        variants = run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode)
     else:
         sim.close()
 
@@ -462,6 +489,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 arithmetic, f64 reductions)",
         "data": "synthetic", "config": dict(config_dict(N, "c64"), parallelism="replicas" if world > 1 else "single"),
+        "path": {"tile_passes": "circuit_run mode %d: %s" % (mode, TILE_MODES[mode]),
+                 "pass_compile_s": round(t_compile, 3)},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "variants": variants,
     }
@@ -504,7 +533,7 @@ def run_profile_case(args):
             recs = wl.random_gate_circuit(N, N_GATES, SEED)
             for _ in range(2):
                 s.reset()
-                s.circuit_run(recs, mode=1)
+                s.circuit_run(recs, mode=args.mode)
             s.expect_xyz()
         else:
             k = args.k
@@ -531,6 +560,9 @@ def main(argv=None):
                     help="run a small workload for a profiler and exit")
     ap.add_argument("--qubits", type=int, default=26)
     ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--mode", type=int, default=1, help="circuit_run mode of the tile profile case")
+    ap.add_argument("--tile-mode", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="circuit_run mode of the timed step (0: 2 when NVRTC loads, else 1)")
     args = ap.parse_args(argv)
     if args.profile_case:
         return run_profile_case(args)

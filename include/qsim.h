@@ -170,14 +170,39 @@ qs_status modmul_table(uint64_t a, uint64_t G, int width, uint32_t* table);
 qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
 
 /* ---- circuits ----------------------------------------------------------- */
-/* Run a gate list in order.  mode 0: one kernel per gate (the per-gate sweep
- * of Sec. 3).  mode 1: the native planner groups consecutive gates into
- * shared-memory tile passes (several gates per read and write of the state;
- * the fusion strategy suggested at the end of Sec. 5.2) and runs each pass as
- * one kernel.  Results equal mode 0 up to floating-point rounding order.
- * gates: host array of n records.  n_passes (may be NULL) receives the
- * number of state sweeps launched. */
+/* Run a gate list.  mode 0: one kernel per gate, in order (the per-gate sweep
+ * of Sec. 3).  Modes 1-3: the native planner groups gates into shared-memory
+ * tile passes (several gates per read and write of the state; the fusion
+ * strategy suggested at the end of Sec. 5.2) and runs each pass as one
+ * kernel.  A pass may take a gate ahead of earlier gates only when it
+ * commutes with all of them (they share no qubit on which either acts
+ * non-diagonally), so the circuit's product is unchanged.  The pass kernel:
+ *   mode 1: the op interpreter compiled into the library;
+ *   mode 2: for QS_C64 states, passes of at most 16 ops run a kernel compiled
+ *           at run time for the pass's op structure (NVRTC, sm_103a; cached
+ *           by structure, the first run of a new structure pays its compile
+ *           time unless circuit_compile ran first); longer passes, and passes
+ *           that fail to compile, use the interpreter;
+ *   mode 3: the compiled kernel for every QS_C64 pass.
+ * Modes 2 and 3 give QS_EUNSUPPORTED on a QS_C64 state when NVRTC cannot be
+ * loaded; QS_C128 states use the interpreter in every tile mode.  Results
+ * equal mode 0 up to floating-point rounding order.  gates: host array of n
+ * records.  n_passes (may be NULL) receives the number of state sweeps
+ * launched.  The paper has no counterpart for modes 1-3. */
 qs_status circuit_run(qs_sim* sim, const qs_gate* gates, int n, int mode, int* n_passes);
+
+/* Plan the tile passes of a QS_C64 circuit on N qubits (13 <= N <= 63) and
+ * compile the kernel of each new pass structure that circuit_run in `mode`
+ * (2 or 3) would launch compiled (host only: no device call; NVRTC must be
+ * loadable, else QS_EUNSUPPORTED).  A later circuit_run of the same circuit
+ * in that mode then launches without compiling.  n_passes (may be NULL)
+ * receives the number of passes planned.  Gate validation as in
+ * circuit_run. */
+qs_status circuit_compile(int N, const qs_gate* gates, int n, int mode, int* n_passes);
+
+/* Whether NVRTC could be loaded (available: 1 or 0) and how many pass
+ * kernels this process has compiled so far (compiles).  Outputs may be NULL. */
+qs_status tile_compiler_info(int* available, long* compiles);
 
 /* As circuit_run, and records a CUDA event pair around every sweep on the
  * handle's stream: pass_ms (host, room for max_passes floats, may be NULL)

@@ -15,7 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqsim.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I" + INCLUDE, "-I" + CSRC]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I" + INCLUDE, "-I" + CSRC,
+         "-I" + BUILD]
 
 
 def nvcc():
@@ -36,10 +37,35 @@ def _compile(src, verbose_ptxas=False):
     return obj, r.stderr
 
 
+JIT_CORE = ("gatekind.h", "cplx.cuh", "tile_core.cuh")
+
+
+def write_jit_core():
+    """The device code that tile passes compiled at run time include, as one
+    C++ string (kJitCore in _build/jit_core.inc): the headers in JIT_CORE
+    with their #include and #pragma once lines dropped."""
+    parts = []
+    for name in JIT_CORE:
+        with open(os.path.join(CSRC, name)) as f:
+            for line in f:
+                t = line.strip()
+                if t.startswith('#include "') or t == "#pragma once":
+                    continue
+                parts.append(line)
+    text = "".join(parts)
+    assert ')QSJIT"' not in text
+    out = os.path.join(BUILD, "jit_core.inc")
+    body = 'static const char kJitCore[] = R"QSJIT(' + text + ')QSJIT";\n'
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
+
+
 def build(force=False, verbose_ptxas=False, quiet=True):
     """Compile every csrc/*.cu for sm_103a and link libqsim.so.  Skips the
     work when the library is newer than every source and header."""
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_core()
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(INCLUDE, "qsim.h"))
@@ -55,7 +81,7 @@ def build(force=False, verbose_ptxas=False, quiet=True):
                 sys.stderr.write(err)
     objs = [o for o, _ in res]
     tmp = LIB + ".tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

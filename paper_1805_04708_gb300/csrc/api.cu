@@ -2,6 +2,7 @@
 // management and dispatch to the kernels.  Every argument is checked on the
 // host before anything is launched.
 #include "internal.cuh"
+#include "tile_jit.h"
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -285,7 +286,7 @@ static qs_status run_gates(qs_sim* s, const qs_gate* gates, int n, int mode, int
                            int max_ev) {
   QS_TRY(check_sim(s));
   CHECK_ARG(n >= 0 && (n == 0 || gates != nullptr), "circuit_run: bad gate list");
-  CHECK_ARG(mode == 0 || mode == 1, "circuit_run: mode %d", mode);
+  CHECK_ARG(mode >= 0 && mode <= 3, "circuit_run: mode %d", mode);
   for (int i = 0; i < n; ++i) QS_TRY(check_gate(s, gates[i]));
   int passes = 0;
   PassTimer timer = {ev, max_ev, 0};
@@ -301,9 +302,31 @@ static qs_status run_gates(qs_sim* s, const qs_gate* gates, int n, int mode, int
       ++passes;
     }
   } else {
-    QS_TRY(run_tile_passes(s, gates, n, &passes, ev ? &timer : nullptr));
+    const int jit = mode == 2 ? 1 : (mode == 3 ? 2 : 0);
+    QS_TRY(run_tile_passes(s, gates, n, &passes, ev ? &timer : nullptr, jit));
   }
   if (n_passes) *n_passes = passes;
+  return QS_OK;
+}
+
+extern "C" qs_status circuit_compile(int N, const qs_gate* gates, int n, int mode, int* n_passes) {
+  CHECK_ARG(mode == 2 || mode == 3, "circuit_compile: mode %d (2 or 3)", mode);
+  CHECK_ARG(N >= tile_bits(QS_C64) && N < 64, "circuit_compile: N = %d must be in %d..63", N, tile_bits(QS_C64));
+  CHECK_ARG(n >= 0 && (n == 0 || gates != nullptr), "circuit_compile: bad gate list");
+  qs_sim probe;
+  probe.N = N;
+  probe.enc = QS_C64;
+  for (int i = 0; i < n; ++i) QS_TRY(check_gate(&probe, gates[i]));
+  if (!tile_jit_available()) {
+    qs_set_error("circuit_compile: NVRTC could not be loaded");
+    return QS_EUNSUPPORTED;
+  }
+  return compile_tile_passes(N, gates, n, n_passes, mode == 3);
+}
+
+extern "C" qs_status tile_compiler_info(int* available, long* compiles) {
+  if (available) *available = tile_jit_available() ? 1 : 0;
+  if (compiles) *compiles = tile_jit_compiles();
   return QS_OK;
 }
 

@@ -1,7 +1,9 @@
 // Complex helpers and the 2x2 update functors shared by the dense-encoding
 // kernels (per-gate sweeps and shared-memory tile passes).
 #pragma once
+#ifndef QS_JIT
 #include <cuda_runtime.h>
+#endif
 
 template <typename R> struct __align__(2 * sizeof(R)) Cx { R x, y; };
 

@@ -55,15 +55,7 @@ static inline size_t qs_amp_bytes(qs_encoding e) {
 // ---------------------------------------------------------------------------
 // gate classification (host)
 // ---------------------------------------------------------------------------
-// Kinds of 2x2 update, each giving the same result as the dense product:
-enum GateKind : int {
-  GK_DENSE = 0,   // general u
-  GK_HAD = 1,     // s * [[1, 1], [1, -1]], s real
-  GK_DIAG = 2,    // diag(d0, d1)
-  GK_ANTI = 3,    // [[0, f01], [f10, 0]]
-  GK_IDENT = 4,   // identity (no-op)
-  GK_REAL = 5     // real dense u (tile passes of complex64 states only)
-};
+#include "gatekind.h"
 // Unit factors multiply exactly: 0 = 1, 1 = i, 2 = -1, 3 = -i, 4 = general.
 struct GateClass {
   int kind;
@@ -111,8 +103,17 @@ struct PassTimer {
 };
 // Number of tile bits used by the tile passes for an encoding.
 int tile_bits(qs_encoding enc);
-// Plan a gate list into tile passes and launch them (gate order preserved).
-qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer);
+// Plan a gate list into tile passes and launch them (the product of the
+// circuit is preserved).  jit: 0 the op interpreter; 1 kernels compiled at run
+// time for the short complex64 passes (the interpreter for the others, and
+// for a pass that fails to compile); 2 compiled kernels for every complex64
+// pass.  jit 1 and 2 give QS_EUNSUPPORTED on a complex64 state when NVRTC
+// cannot be loaded.
+qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer, int jit);
+// Plan the complex64 passes of an N-qubit circuit and compile each (host
+// only; the compiled kernels are cached for later launches): all passes when
+// all_passes, else those that mode 1 would run compiled.
+qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes);
 
 // ADAPT2 --------------------------------------------------------------------------
 // Device-resident range of the adaptive encoding (Sec. 4.1): the current

@@ -18,472 +18,19 @@
 // outside the tile is a per-tile condition).  Gate order is kept, so the
 // result equals the per-gate sweep up to rounding order.
 #include "internal.cuh"
-#include "cplx.cuh"
+#include "tile_core.cuh"
+#include "tile_jit.h"
 #include <string.h>
 #include <stdlib.h>
+#include <vector>
+
+using namespace qs_tile;
 
 namespace {
 
-constexpr int TPB = 256;      // 8 warps
-constexpr int LANE_BITS = 5;  // local bits 1..5
-constexpr int WARP_BITS = 3;
-constexpr int MAX_TOPS = 96;
-constexpr int LOW_BITS = 4;   // index bits always in the tile (16-amplitude runs)
-
-enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5 };
-
-struct TOp {
-  uint8_t type, kind, c0, c1;
-  uint8_t a;           // T_REG / T_DIAG_REG: register slot; T_LANE: lane bit; T_DIAG_THR: local bit
-  uint8_t pad[3];
-  uint32_t smask;      // control bits among the register slots (bits of j)
-  uint32_t tmask;      // control bits among lane / warp local bits (local-index mask)
-  uint64_t gmask;      // control bits outside the tile
-  uint64_t gtbit;      // T_DIAG_OUT: the target bit (global)
-  float uf[8];
-  double ud[8];
-};
-struct TMap {
-  uint8_t reg[8];      // local bit of register slot s (reg[0] = 0)
-  uint8_t warp[4];     // local bit of warp bit k
-};
-
-struct TileParams2 {
-  int N, b;
-  uint64_t out_mask;   // global bits outside the tile
-  uint8_t gpos[20];    // global position of local bit k
-  TMap init, fin;      // register / warp assignment at load and at store
-  int nops;
-  int last_xpose;      // index of the last transpose op, -1 if none
-  TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
-  TMap maps[16];
-};
-
-__device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
-  uint64_t r = 0;
-  for (uint64_t m = mask; m; m &= m - 1) {
-    if (x & 1) r |= m & (~m + 1);
-    x >>= 1;
-  }
-  return r;
-}
-
-template <typename R> __device__ __forceinline__ Cx<R> ucx(const TOp& o, int k);
-template <> __device__ __forceinline__ Cx<float> ucx<float>(const TOp& o, int k) { return cx<float>(o.uf[2 * k], o.uf[2 * k + 1]); }
-template <> __device__ __forceinline__ Cx<double> ucx<double>(const TOp& o, int k) { return cx<double>(o.ud[2 * k], o.ud[2 * k + 1]); }
-
-// local index of register j under map m, given the thread part tl
-template <int RB>
-__device__ __forceinline__ uint32_t lidx(const TMap& m, int j, uint32_t tl) {
-  uint32_t l = tl;
-#pragma unroll
-  for (int s = 0; s < RB; ++s)
-    if ((j >> s) & 1) l |= 1u << m.reg[s];
-  return l;
-}
-__device__ __forceinline__ uint32_t thread_part(const TMap& m, int lane, int warp) {
-  uint32_t l = (uint32_t)lane << 1;
-#pragma unroll
-  for (int k = 0; k < WARP_BITS; ++k)
-    if ((warp >> k) & 1) l |= 1u << m.warp[k];
-  return l;
-}
-// global offset (within the tile) of a local index: local bits 0..3 are
-// index bits 0..3, the others map through gpos
-__device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b) {
-  uint64_t g = l & 15u;
-  for (int k = 4; k < b; ++k)
-    if ((l >> k) & 1) g |= 1ull << gpos[k];
-  return g;
-}
-
-// --- register-slot pair op, slot S fixed at compile time -----------------------------
-template <typename R, int RB, int S, typename F>
-__device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) {
-  if (smask == 0) {   // the common case: no control among the register slots
-#pragma unroll
-    for (int j = 0; j < (1 << RB); ++j)
-      if (!((j >> S) & 1)) f.pair(v[j], v[j | (1 << S)]);
-  } else {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); ++j) {
-      if ((j >> S) & 1) continue;
-      if ((j & (int)smask) != (int)smask) continue;
-      f.pair(v[j], v[j | (1 << S)]);
-    }
-  }
-}
-
-// diagonal on register slot S: factor d1 where bit S is 1, d0 where it is 0;
-// skip0 / skip1 leave the elements with a unit factor untouched
-template <typename R, int RB, int S>
-__device__ __forceinline__ void reg_diag(Cx<R>* v, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
-  if (smask == 0) {
-#pragma unroll
-    for (int j = 0; j < (1 << RB); ++j) {
-      const bool one = (j >> S) & 1;
-      if (one ? skip1 : skip0) continue;
-      v[j] = cmul_code(v[j], one ? d1 : d0, 4);
-    }
-    return;
-  }
-#pragma unroll
-  for (int j = 0; j < (1 << RB); ++j) {
-    if ((j & (int)smask) != (int)smask) continue;
-    const bool one = (j >> S) & 1;
-    if (one ? skip1 : skip0) continue;
-    v[j] = cmul_code(v[j], one ? d1 : d0, 4);
-  }
-}
-template <typename R, int RB>
-__device__ __forceinline__ void reg_diag_rt(Cx<R>* v, int s, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
-  switch (s) {
-    case 0: reg_diag<R, RB, 0>(v, smask, d0, d1, skip0, skip1); break;
-    case 1: reg_diag<R, RB, (RB > 1 ? 1 : 0)>(v, smask, d0, d1, skip0, skip1); break;
-    case 2: reg_diag<R, RB, (RB > 2 ? 2 : 0)>(v, smask, d0, d1, skip0, skip1); break;
-    case 3: reg_diag<R, RB, (RB > 3 ? 3 : 0)>(v, smask, d0, d1, skip0, skip1); break;
-    default: reg_diag<R, RB, (RB > 4 ? 4 : 0)>(v, smask, d0, d1, skip0, skip1); break;
-  }
-}
-template <typename R, int RB, typename F>
-__device__ __forceinline__ void reg_op(Cx<R>* v, int s, uint32_t smask, const F& f) {
-  switch (s) {
-    case 0: reg_pairs<R, RB, 0>(v, smask, f); break;
-    case 1: if (RB > 1) reg_pairs<R, RB, (RB > 1 ? 1 : 0)>(v, smask, f); break;
-    case 2: if (RB > 2) reg_pairs<R, RB, (RB > 2 ? 2 : 0)>(v, smask, f); break;
-    case 3: if (RB > 3) reg_pairs<R, RB, (RB > 3 ? 3 : 0)>(v, smask, f); break;
-    case 4: if (RB > 4) reg_pairs<R, RB, (RB > 4 ? 4 : 0)>(v, smask, f); break;
-    default: if (RB > 5) reg_pairs<R, RB, (RB > 5 ? 5 : 0)>(v, smask, f); break;
-  }
-}
-
-template <typename R> __device__ __forceinline__ R uscal(const TOp& o) {
-  if constexpr (sizeof(R) == 4) return o.uf[0]; else return o.ud[0];
-}
-
-template <typename R> __device__ __forceinline__ R shx(R x, int m);
-template <> __device__ __forceinline__ float shx<float>(float x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
-template <> __device__ __forceinline__ double shx<double>(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
-
-// lane-bit op: partner values by shuffle, each lane keeps its own output
-template <typename R, int RB, bool SWAP>
-__device__ __forceinline__ void lane_op(Cx<R>* v, const TOp& o, int lane, bool tok) {
-  const int m = 1 << o.a;
-  const bool hi = (lane >> o.a) & 1;
-  Cx<R> u00 = ucx<R>(o, 0), u01 = ucx<R>(o, 1), u10 = ucx<R>(o, 2), u11 = ucx<R>(o, 3);
-  if constexpr (sizeof(R) == 4) {
-    if (SWAP && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) {
-      // pure swap: every lane takes its partner's value
-#pragma unroll
-      for (int j = 0; j < (1 << RB); ++j) {
-        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
-        if (tok && (j & (int)o.smask) == (int)o.smask) v[j] = p;
-      }
-      return;
-    }
-    if (o.kind == GK_REAL) {
-      // real coefficients: packed FP32x2 on (re, im)
-      const float2 cs = hi ? make_float2(o.uf[6], o.uf[6]) : make_float2(o.uf[0], o.uf[0]);
-      const float2 cp = hi ? make_float2(o.uf[4], o.uf[4]) : make_float2(o.uf[2], o.uf[2]);
-      const bool all = tok && o.smask == 0;
-#pragma unroll
-      for (int j = 0; j < (1 << RB); ++j) {
-        const float2 p = make_float2(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
-        if (!all && (!tok || (j & (int)o.smask) != (int)o.smask)) continue;
-#ifdef QS_HAVE_F32X2
-        const float2 r = __ffma2_rn(cs, make_float2(v[j].x, v[j].y), __fmul2_rn(cp, p));
-#else
-        const float2 r = make_float2(fmaf(cs.x, v[j].x, cp.x * p.x), fmaf(cs.x, v[j].y, cp.x * p.y));
-#endif
-        v[j] = cx<R>(r.x, r.y);
-      }
-      return;
-    }
-    // each lane keeps cs * own + cp * partner, with per-lane coefficients
-    const Cx<R> cs = hi ? u11 : u00, cp = hi ? u10 : u01;
-    if (o.smask == 0) {
-#pragma unroll
-      for (int j = 0; j < (1 << RB); ++j) {
-        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
-        if (tok) v[j] = cmac2(cs, v[j], cp, p);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < (1 << RB); ++j) {
-        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
-        if (tok && (j & (int)o.smask) == (int)o.smask) v[j] = cmac2(cs, v[j], cp, p);
-      }
-    }
-    return;
-  }
-#pragma unroll
-  for (int j = 0; j < (1 << RB); ++j) {
-    Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
-    if (!tok || (j & (int)o.smask) != (int)o.smask) continue;
-    Cx<R> a0 = hi ? p : v[j], a1 = hi ? v[j] : p;
-    switch (o.kind) {
-      case GK_HAD: {
-        const R s = uscal<R>(o);
-        v[j] = hi ? cx<R>((a0.x - a1.x) * s, (a0.y - a1.y) * s) : cx<R>((a0.x + a1.x) * s, (a0.y + a1.y) * s);
-        break;
-      }
-      case GK_ANTI:
-        v[j] = hi ? cmul_code(a0, u10, o.c1) : cmul_code(a1, u01, o.c0);
-        break;
-      case GK_DIAG:
-        v[j] = hi ? cmul_code(a1, u11, o.c1) : cmul_code(a0, u00, o.c0);
-        break;
-      default:
-        v[j] = hi ? cmac2(u10, a0, u11, a1) : cmac2(u00, a0, u01, a1);
-    }
-  }
-}
-
-template <typename R, int RB>
-__device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
-                                          int lane) {
-  if constexpr (sizeof(R) == 4) {
-    const float4* s4 = (const float4*)s;
-#pragma unroll
-    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-      float4 x = s4[(base + woff + roff[jj]) >> 1];
-      v[2 * jj] = cx<float>(x.x, x.y);
-      v[2 * jj + 1] = cx<float>(x.z, x.w);
-    }
-  } else {
-    const double2* s2 = (const double2*)s;
-#pragma unroll
-    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-      const uint64_t g = base + woff + roff[jj];
-      double2 x = s2[g], y = s2[g + 1];
-      v[2 * jj] = cx<double>(x.x, x.y);
-      v[2 * jj + 1] = cx<double>(y.x, y.y);
-    }
-  }
-}
-template <typename R, int RB>
-__device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
-                                           int lane) {
-  if constexpr (sizeof(R) == 4) {
-    float4* s4 = (float4*)s;
-#pragma unroll
-    for (int jj = 0; jj < (1 << (RB - 1)); ++jj)
-      s4[(base + woff + roff[jj]) >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
-  } else {
-    double2* s2 = (double2*)s;
-#pragma unroll
-    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-      const uint64_t g = base + woff + roff[jj];
-      s2[g] = make_double2(v[2 * jj].x, v[2 * jj].y);
-      s2[g + 1] = make_double2(v[2 * jj + 1].x, v[2 * jj + 1].y);
-    }
-  }
-}
-
-// FEAT: which specialised complex64 paths the pass needs (bit 0: swaps, bit 1:
-// Hadamard-shaped); passes without them run a smaller kernel.
-constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_HAD: real-matrix path (packed FP32x2)
-
-// 16-byte global -> shared copies that bypass registers (LDGSTS), so the next
-// tile's loads are in flight while the current tile is computed and stored.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Each thread stages exactly the 16-byte chunks it will read back, so the
-// stage buffer needs no barrier: the thread's own wait_group orders it.
-template <typename R, int RB>
-__device__ __forceinline__ void stage_tile(const void* s, Cx<R>* st, uint64_t base, const uint64_t* roff, uint64_t woff,
-                                           const TMap& m, uint32_t tl) {
-#pragma unroll
-  for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
-    const uint64_t g = base + woff + roff[jj];
-    if constexpr (sizeof(R) == 4) {
-      cp_async16(((float4*)st) + (l >> 1), ((const float4*)s) + (g >> 1));
-    } else {
-      cp_async16(st + l, ((const double2*)s) + g);
-      cp_async16(st + l + 1, ((const double2*)s) + g + 1);
-    }
-  }
-  cp_async_commit();
-}
-template <typename R, int RB>
-__device__ __forceinline__ void unstage_tile(const Cx<R>* st, Cx<R>* v, const TMap& m, uint32_t tl) {
-#pragma unroll
-  for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
-    if constexpr (sizeof(R) == 4) {
-      const float4 x = ((const float4*)st)[l >> 1];
-      v[2 * jj] = cx<float>(x.x, x.y);
-      v[2 * jj + 1] = cx<float>(x.z, x.w);
-    } else {
-      v[2 * jj] = st[l];
-      v[2 * jj + 1] = st[l + 1];
-    }
-  }
-}
-
 template <typename R, int RB, int FEAT>
 __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __grid_constant__ TileParams2 P) {
-  extern __shared__ unsigned char smraw[];
-  constexpr int NR = 1 << RB;
-  // global offsets of the register part (pairs jj: slots 1..RB-1) at load / store
-  uint64_t* roff_in = (uint64_t*)smraw;
-  uint64_t* roff_out = roff_in + NR / 2;
-  // transpose buffer, 2^b elements; between the last transpose of a tile and
-  // the start of the next it stages the next tile
-  Cx<R>* xb = (Cx<R>*)(smraw + NR * sizeof(uint64_t));
-  Cx<R>* stg = xb;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x < NR / 2) {
-    roff_in[threadIdx.x] = goff(lidx<RB>(P.init, 2 * threadIdx.x, 0), P.gpos, P.b);
-    roff_out[threadIdx.x] = goff(lidx<RB>(P.fin, 2 * threadIdx.x, 0), P.gpos, P.b);
-  }
-  __syncthreads();
-  const uint64_t woff_in = goff(thread_part(P.init, lane, warp), P.gpos, P.b);
-  const uint64_t woff_out = goff(thread_part(P.fin, lane, warp), P.gpos, P.b);
-  const uint32_t tl_in = thread_part(P.init, lane, warp);
-  const uint64_t ntiles = 1ull << (P.N - P.b);
-  Cx<R> v[NR];
-  if (blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
-  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
-    const uint64_t base = deposit_t(tau, P.out_mask);
-    cp_async_wait_all();
-    unstage_tile<R, RB>(stg, v, P.init, tl_in);
-    const uint64_t nxt = tau + gridDim.x;
-    if (P.last_xpose < 0 && nxt < ntiles)
-      stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
-    TMap cur = P.init;
-    uint32_t tl = thread_part(cur, lane, warp);
-    Cx<R> fac = cx<R>((R)1, (R)0);
-    int mapi = 0;
-    for (int i = 0; i < P.nops; ++i) {
-      const TOp& o = P.ops[i];
-      if (o.type == T_XPOSE) {
-        // write every register at its local index, read back under the new map
-#pragma unroll
-        for (int jj = 0; jj < NR / 2; ++jj) {
-          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
-          if constexpr (sizeof(R) == 4) {
-            ((float4*)xb)[l >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
-          } else {
-            xb[l] = v[2 * jj];
-            xb[l + 1] = v[2 * jj + 1];
-          }
-        }
-        __syncthreads();
-        cur = P.maps[mapi++];
-        tl = thread_part(cur, lane, warp);
-#pragma unroll
-        for (int jj = 0; jj < NR / 2; ++jj) {
-          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
-          if constexpr (sizeof(R) == 4) {
-            float4 x = ((const float4*)xb)[l >> 1];
-            v[2 * jj] = cx<float>(x.x, x.y);
-            v[2 * jj + 1] = cx<float>(x.z, x.w);
-          } else {
-            v[2 * jj] = xb[l];
-            v[2 * jj + 1] = xb[l + 1];
-          }
-        }
-        __syncthreads();
-        if (i == P.last_xpose && nxt < ntiles)
-          stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
-        continue;
-      }
-      const bool gok = (base & o.gmask) == o.gmask;       // outer controls
-      const bool tok = (tl & o.tmask) == o.tmask;         // lane / warp controls
-      if (o.pad[0] != 0) {
-        // folded run of per-thread diagonals: multiply the factor, apply at the end
-        if (gok && tok) {
-          const bool one = (o.type == T_DIAG_THR) ? ((tl >> o.a) & 1) : ((base & o.gtbit) != 0);
-          if ((one ? o.c1 : o.c0) != 0) fac = cmul_code(fac, ucx<R>(o, one ? 3 : 0), 4);
-        }
-        if (o.pad[0] == 2) {
-          if (fac.x != (R)1 || fac.y != (R)0) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) v[j] = cmul_code(v[j], fac, 4);
-          }
-          fac = cx<R>((R)1, (R)0);
-        }
-        continue;
-      }
-      if (!gok) continue;
-      switch (o.type) {
-        case T_REG: {
-          if (!tok) break;
-          if constexpr (sizeof(R) == 4) {
-            // complex64: Hadamard-shaped or dense (exact for the unit entries
-            // of X, Y, CNOT, TOFFOLI)
-            // (a register-slot swap as renames makes the register allocation
-            // spill at 128 registers; swaps on register slots stay dense)
-            if ((FEAT & FEAT_HAD) && o.kind == GK_REAL) {
-              OpRealF f;
-              f.u00 = make_float2(o.uf[0], o.uf[0]); f.u01 = make_float2(o.uf[2], o.uf[2]);
-              f.u10 = make_float2(o.uf[4], o.uf[4]); f.u11 = make_float2(o.uf[6], o.uf[6]);
-              reg_op<R, RB>(v, o.a, o.smask, f);
-            } else {
-              OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
-              reg_op<R, RB>(v, o.a, o.smask, f);
-            }
-          } else {
-            // complex128: the FP64 pipe is the bound, so keep the cheaper forms
-            switch (o.kind) {
-              case GK_HAD: { OpHad<R> f; f.s = uscal<R>(o); reg_op<R, RB>(v, o.a, o.smask, f); break; }
-              case GK_ANTI: { OpAnti<R> f; f.f01 = ucx<R>(o, 1); f.f10 = ucx<R>(o, 2); f.c0 = o.c0; f.c1 = o.c1; reg_op<R, RB>(v, o.a, o.smask, f); break; }
-              default: {
-                OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
-                reg_op<R, RB>(v, o.a, o.smask, f);
-              }
-            }
-          }
-          break;
-        }
-        case T_LANE:
-          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0>(v, o, lane, tok);
-          break;
-        case T_DIAG_REG:
-        case T_DIAG_THR:
-        case T_DIAG_OUT: {
-          if (!tok) break;
-          const Cx<R> d0 = ucx<R>(o, 0), d1 = ucx<R>(o, 3);
-          if (o.type == T_DIAG_REG) {
-            if constexpr (sizeof(R) == 4) {
-              reg_diag_rt<R, RB>(v, o.a, o.smask, d0, d1, o.c0 == 0, o.c1 == 0);
-            } else {
-              const int sl = o.a;
-#pragma unroll
-              for (int j = 0; j < NR; ++j) {
-                if ((j & (int)o.smask) != (int)o.smask) continue;
-                const bool one = (j >> sl) & 1;
-                v[j] = one ? cmul_code(v[j], d1, o.c1) : cmul_code(v[j], d0, o.c0);
-              }
-            }
-          } else {
-            const bool one = (o.type == T_DIAG_THR) ? ((tl >> o.a) & 1) : ((base & o.gtbit) != 0);
-            const int code = one ? o.c1 : o.c0;
-            if (code == 0) break;
-            const Cx<R> d = one ? d1 : d0;
-            if (o.smask == 0) {
-#pragma unroll
-              for (int j = 0; j < NR; ++j) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
-            } else {
-#pragma unroll
-              for (int j = 0; j < NR; ++j)
-                if ((j & (int)o.smask) == (int)o.smask) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
-            }
-          }
-          break;
-        }
-        default: break;
-      }
-    }
-    store_tile<R, RB>(s, v, base, roff_out, woff_out, lane);
-  }
+  tile_pass<R, RB, FEAT, ProgRT>(s, P);
 }
 
 }  // namespace
@@ -761,6 +308,26 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
 int tile_register_bits(qs_encoding enc) { return enc == QS_C128 ? 4 : 5; }
 int tile_bits(qs_encoding enc) { return tile_register_bits(enc) + LANE_BITS + WARP_BITS; }
 
+// Where planned passes go: launched on a handle's stream (interpreter or
+// compiled kernel), or only compiled (no device work).
+struct PassSink {
+  qs_sim* s;            // null: compile only
+  int N;
+  qs_encoding enc;
+  int jit;              // 0: interpreter; 1: compiled kernels for passes of at
+                        // most TILE_JIT_MAX_OPS ops, else the interpreter;
+                        // 2: compiled kernels for every pass (complex64)
+  PassTimer* timer;
+  int emitted;
+  std::vector<TileParams2>* collect;   // compile only: the passes to compile
+};
+// A compiled pass is straight-line code whose length grows with its op count;
+// measured on GB300 at N = 30 it beats the interpreter up to about 16 ops and
+// loses beyond, where the unrolled code outgrows the instruction cache.
+constexpr int TILE_JIT_MAX_OPS = 16;
+
+static qs_status emit_pass(PassSink& k, const TileParams2& P);
+
 // Pass packing.  Each pass takes gates in circuit order while the union of
 // their non-diagonal targets fits the tile; a gate that does not fit is left
 // for a later pass, and so is every later gate that does not commute with a
@@ -770,12 +337,11 @@ int tile_bits(qs_encoding enc) { return tile_register_bits(enc) + LANE_BITS + WA
 // qubits inside each block.  Every gate a pass takes therefore commutes with
 // all the earlier gates it overtakes, and the product equals the circuit's.
 // A pass whose op list overflows is split.
-static qs_status run_pass(qs_sim* s, const qs_gate* gates, const int* gidx, int ng, uint64_t tile, int* launched,
-                          PassTimer* timer);
+static qs_status run_pass(PassSink& k, const qs_gate* gates, const int* gidx, int ng, uint64_t tile);
 
-qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer) {
-  const int b = tile_bits(s->enc);
-  const int N = s->N;
+static qs_status plan_tile_passes(PassSink& k, const qs_gate* gates, int n) {
+  const int b = tile_bits(k.enc);
+  const int N = k.N;
   // per gate: qubits acted on non-diagonally (X) and diagonally (Z)
   int* gidx = (int*)malloc(sizeof(int) * (size_t)(n + 1));
   int* rem = (int*)malloc(sizeof(int) * (size_t)(n + 1));
@@ -800,14 +366,13 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
   // A transpose costs about a third of a sweep, so a pass takes only as many
   // high targets as the lanes and register slots hold (no transposes); the
   // warp bits are padding.
-  const int max_targets = LOW_BITS + 2 + (tile_register_bits(s->enc) - 1);
-  int launched = 0;
+  const int max_targets = LOW_BITS + 2 + (tile_register_bits(k.enc) - 1);
   qs_status st = QS_OK;
   while (nrem > 0 && st == QS_OK) {
     uint64_t S = low, bx = 0, bz = 0;
     int ng = 0, nleft = 0;
-    for (int k = 0; k < nrem; ++k) {
-      const int i = rem[k];
+    for (int j = 0; j < nrem; ++j) {
+      const int i = rem[j];
       const bool blocked = (xq[i] & (bx | bz)) != 0 || ((xq[i] | zq[i]) & bx) != 0;
       if (!blocked && __builtin_popcountll(S | xq[i]) <= max_targets && ng < MAX_TOPS / 2) {
         S |= xq[i];
@@ -824,19 +389,45 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
     // constants (a diagonal folds into one factor), inside it they cost
     // per-element work
     uint64_t used = 0;
-    for (int k = 0; k < ng; ++k) used |= xq[gidx[k]] | zq[gidx[k]];
+    for (int j = 0; j < ng; ++j) used |= xq[gidx[j]] | zq[gidx[j]];
     uint64_t tile = S;
     for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q)
       if (!((used >> q) & 1)) tile |= 1ull << q;
     for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
-    st = run_pass(s, gates, gidx, ng, tile, &launched, timer);
+    st = run_pass(k, gates, gidx, ng, tile);
   }
   free(gidx); free(rem); free(xq); free(zq);
-  if (n_passes) *n_passes = launched;
   return st;
 }
 
-static qs_status launch_pass(qs_sim* s, const TileParams2& P, PassTimer* timer) {
+qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer, int jit) {
+  PassSink k = {s, s->N, s->enc, 0, timer, 0, nullptr};
+  if (s->enc == QS_C64 && jit != 0) {
+    if (!tile_jit_available()) {
+      qs_set_error("circuit_run: compiled tile passes need NVRTC, which could not be loaded");
+      return QS_EUNSUPPORTED;
+    }
+    k.jit = jit;
+  }
+  const qs_status st = plan_tile_passes(k, gates, n);
+  if (n_passes) *n_passes = k.emitted;
+  return st;
+}
+
+qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes) {
+  std::vector<TileParams2> passes;
+  PassSink k = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes};
+  QS_TRY(plan_tile_passes(k, gates, n));
+  if (n_passes) *n_passes = k.emitted;
+  return tile_jit_compile_all(passes);
+}
+
+static qs_status launch_pass(PassSink& k, const TileParams2& P) {
+  qs_sim* s = k.s;
+  // automatic choice: a pass that fails to compile runs on the interpreter
+  bool jit_ok = true;
+  if (k.jit == 1 && s->enc == QS_C64 && P.nops <= TILE_JIT_MAX_OPS) jit_ok = tile_jit_compile(P) == QS_OK;
+  PassTimer* timer = k.timer;
   const bool timed = timer && timer->n < timer->max_ev;
   if (timed) QS_CUDA(cudaEventRecord(timer->ev[2 * timer->n], s->stream));
   const uint64_t ntiles = 1ull << (s->N - P.b);
@@ -846,6 +437,9 @@ static qs_status launch_pass(qs_sim* s, const TileParams2& P, PassTimer* timer) 
     const size_t smem = ((size_t)16 << P.b) + 16 * sizeof(uint64_t);
     QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
+  } else if (k.jit == 2 || (k.jit == 1 && P.nops <= TILE_JIT_MAX_OPS && jit_ok)) {
+    const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
+    QS_TRY(tile_jit_launch(s, P, grid, smem));
   } else {
     int feat = 0;
     for (int i = 0; i < P.nops; ++i) {
@@ -876,17 +470,22 @@ static qs_status launch_pass(qs_sim* s, const TileParams2& P, PassTimer* timer) 
   return QS_OK;
 }
 
-static qs_status run_pass(qs_sim* s, const qs_gate* gates, const int* gidx, int ng, uint64_t tile, int* launched,
-                          PassTimer* timer) {
-  static thread_local TileParams2 P;
-  const int b = tile_bits(s->enc);
-  if (build_pass(gates, gidx, ng, s->N, b, tile_register_bits(s->enc), tile, &P, s->enc == QS_C64)) {
-    QS_TRY(launch_pass(s, P, timer));
-    ++*launched;
+static qs_status emit_pass(PassSink& k, const TileParams2& P) {
+  ++k.emitted;
+  if (!k.s) {
+    if (k.jit == 2 || P.nops <= TILE_JIT_MAX_OPS) k.collect->push_back(P);
     return QS_OK;
   }
+  return launch_pass(k, P);
+}
+
+static qs_status run_pass(PassSink& k, const qs_gate* gates, const int* gidx, int ng, uint64_t tile) {
+  static thread_local TileParams2 P;
+  const int b = tile_bits(k.enc);
+  if (build_pass(gates, gidx, ng, k.N, b, tile_register_bits(k.enc), tile, &P, k.enc == QS_C64))
+    return emit_pass(k, P);
   // too many ops for one launch: split the gate run in halves (same tile)
   const int h = ng / 2;
-  QS_TRY(run_pass(s, gates, gidx, h, tile, launched, timer));
-  return run_pass(s, gates, gidx + h, ng - h, tile, launched, timer);
+  QS_TRY(run_pass(k, gates, gidx, h, tile));
+  return run_pass(k, gates, gidx + h, ng - h, tile);
 }

@@ -1,0 +1,519 @@
+// Tile passes: several gates per read and write of the state (the gate
+// fusion that the end of Sec. 5.2 proposes to raise arithmetic intensity;
+// every gate keeps its own 2x2 matrix, the fusion is in the data movement).
+//
+// A tile is the 2^b amplitudes whose index bits outside the tile bit set are
+// fixed; the set holds the low 6 index bits (512-byte runs) plus the targets
+// of the pass's gates.  Inside a CTA of 256 threads the b local bits are
+// split three ways:
+//   local bit 0 and RB-1 more local bits  -> register slots (2^RB amplitudes
+//                                             per thread, updated in registers)
+//   local bits 1..5                         -> the 32 lanes (updated with one
+//                                             warp shuffle per amplitude)
+//   the remaining 3 local bits              -> the 8 warps
+// A gate on a register bit or a lane bit runs without shared memory; a gate on
+// a warp bit first swaps that bit into a register slot by one shared-memory
+// transpose.  Diagonal gates run in place whatever their target (the target
+// bit is known for every element), and controls may be any bit (a control
+// outside the tile is a per-tile condition).  Gate order is kept, so the
+// result equals the per-gate sweep up to rounding order.
+//
+// This header holds the device side: it is compiled into the library (the
+// op interpreter, k_tile.cu) and, as source text, into the passes compiled at
+// run time (tile_jit.cu), so it includes nothing when QS_JIT is defined.
+#pragma once
+#ifndef QS_JIT
+#include <cuda_runtime.h>
+#include <stdint.h>
+#endif
+#include "gatekind.h"
+#include "cplx.cuh"
+
+namespace qs_tile {
+
+constexpr int TPB = 256;      // 8 warps
+constexpr int LANE_BITS = 5;  // local bits 1..5
+constexpr int WARP_BITS = 3;
+constexpr int MAX_TOPS = 96;
+constexpr int LOW_BITS = 4;   // index bits always in the tile (16-amplitude runs)
+
+enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5 };
+
+struct TOp {
+  uint8_t type, kind, c0, c1;
+  uint8_t a;           // T_REG / T_DIAG_REG: register slot; T_LANE: lane bit; T_DIAG_THR: local bit
+  uint8_t pad[3];
+  uint32_t smask;      // control bits among the register slots (bits of j)
+  uint32_t tmask;      // control bits among lane / warp local bits (local-index mask)
+  uint64_t gmask;      // control bits outside the tile
+  uint64_t gtbit;      // T_DIAG_OUT: the target bit (global)
+  float uf[8];
+  double ud[8];
+};
+struct TMap {
+  uint8_t reg[8];      // local bit of register slot s (reg[0] = 0)
+  uint8_t warp[4];     // local bit of warp bit k
+};
+
+struct TileParams2 {
+  int N, b;
+  uint64_t out_mask;   // global bits outside the tile
+  uint8_t gpos[20];    // global position of local bit k
+  TMap init, fin;      // register / warp assignment at load and at store
+  int nops;
+  int last_xpose;      // index of the last transpose op, -1 if none
+  TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
+  TMap maps[16];
+};
+
+__device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
+  uint64_t r = 0;
+  for (uint64_t m = mask; m; m &= m - 1) {
+    if (x & 1) r |= m & (~m + 1);
+    x >>= 1;
+  }
+  return r;
+}
+
+template <typename R> __device__ __forceinline__ Cx<R> ucx(const TOp& o, int k);
+template <> __device__ __forceinline__ Cx<float> ucx<float>(const TOp& o, int k) { return cx<float>(o.uf[2 * k], o.uf[2 * k + 1]); }
+template <> __device__ __forceinline__ Cx<double> ucx<double>(const TOp& o, int k) { return cx<double>(o.ud[2 * k], o.ud[2 * k + 1]); }
+
+// local index of register j under map m, given the thread part tl
+template <int RB>
+__device__ __forceinline__ uint32_t lidx(const TMap& m, int j, uint32_t tl) {
+  uint32_t l = tl;
+#pragma unroll
+  for (int s = 0; s < RB; ++s)
+    if ((j >> s) & 1) l |= 1u << m.reg[s];
+  return l;
+}
+__device__ __forceinline__ uint32_t thread_part(const TMap& m, int lane, int warp) {
+  uint32_t l = (uint32_t)lane << 1;
+#pragma unroll
+  for (int k = 0; k < WARP_BITS; ++k)
+    if ((warp >> k) & 1) l |= 1u << m.warp[k];
+  return l;
+}
+// global offset (within the tile) of a local index: local bits 0..3 are
+// index bits 0..3, the others map through gpos
+__device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b) {
+  uint64_t g = l & 15u;
+  for (int k = 4; k < b; ++k)
+    if ((l >> k) & 1) g |= 1ull << gpos[k];
+  return g;
+}
+
+// --- register-slot pair op, slot S fixed at compile time -----------------------------
+template <typename R, int RB, int S, typename F>
+__device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) {
+  if (smask == 0) {   // the common case: no control among the register slots
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j)
+      if (!((j >> S) & 1)) f.pair(v[j], v[j | (1 << S)]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+      if ((j >> S) & 1) continue;
+      if ((j & (int)smask) != (int)smask) continue;
+      f.pair(v[j], v[j | (1 << S)]);
+    }
+  }
+}
+
+// diagonal on register slot S: factor d1 where bit S is 1, d0 where it is 0;
+// skip0 / skip1 leave the elements with a unit factor untouched
+template <typename R, int RB, int S>
+__device__ __forceinline__ void reg_diag(Cx<R>* v, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
+  if (smask == 0) {
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+      const bool one = (j >> S) & 1;
+      if (one ? skip1 : skip0) continue;
+      v[j] = cmul_code(v[j], one ? d1 : d0, 4);
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    if ((j & (int)smask) != (int)smask) continue;
+    const bool one = (j >> S) & 1;
+    if (one ? skip1 : skip0) continue;
+    v[j] = cmul_code(v[j], one ? d1 : d0, 4);
+  }
+}
+template <typename R, int RB>
+__device__ __forceinline__ void reg_diag_rt(Cx<R>* v, int s, uint32_t smask, Cx<R> d0, Cx<R> d1, bool skip0, bool skip1) {
+  switch (s) {
+    case 0: reg_diag<R, RB, 0>(v, smask, d0, d1, skip0, skip1); break;
+    case 1: reg_diag<R, RB, (RB > 1 ? 1 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+    case 2: reg_diag<R, RB, (RB > 2 ? 2 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+    case 3: reg_diag<R, RB, (RB > 3 ? 3 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+    default: reg_diag<R, RB, (RB > 4 ? 4 : 0)>(v, smask, d0, d1, skip0, skip1); break;
+  }
+}
+template <typename R, int RB, typename F>
+__device__ __forceinline__ void reg_op(Cx<R>* v, int s, uint32_t smask, const F& f) {
+  switch (s) {
+    case 0: reg_pairs<R, RB, 0>(v, smask, f); break;
+    case 1: if (RB > 1) reg_pairs<R, RB, (RB > 1 ? 1 : 0)>(v, smask, f); break;
+    case 2: if (RB > 2) reg_pairs<R, RB, (RB > 2 ? 2 : 0)>(v, smask, f); break;
+    case 3: if (RB > 3) reg_pairs<R, RB, (RB > 3 ? 3 : 0)>(v, smask, f); break;
+    case 4: if (RB > 4) reg_pairs<R, RB, (RB > 4 ? 4 : 0)>(v, smask, f); break;
+    default: if (RB > 5) reg_pairs<R, RB, (RB > 5 ? 5 : 0)>(v, smask, f); break;
+  }
+}
+
+template <typename R> __device__ __forceinline__ R uscal(const TOp& o) {
+  if constexpr (sizeof(R) == 4) return o.uf[0]; else return o.ud[0];
+}
+
+template <typename R> __device__ __forceinline__ R shx(R x, int m);
+template <> __device__ __forceinline__ float shx<float>(float x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+template <> __device__ __forceinline__ double shx<double>(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+
+// lane-bit op: partner values by shuffle, each lane keeps its own output
+template <typename R, int RB, bool SWAP, class OS>
+__device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, int lane, bool tok) {
+  const int m = 1 << st.a;
+  const bool hi = (lane >> st.a) & 1;
+  Cx<R> u00 = ucx<R>(o, 0), u01 = ucx<R>(o, 1), u10 = ucx<R>(o, 2), u11 = ucx<R>(o, 3);
+  if constexpr (sizeof(R) == 4) {
+    if (SWAP && st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0) {
+      // pure swap: every lane takes its partner's value
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (tok && (j & (int)st.smask) == (int)st.smask) v[j] = p;
+      }
+      return;
+    }
+    if (st.kind == GK_REAL) {
+      // real coefficients: packed FP32x2 on (re, im)
+      const float2 cs = hi ? make_float2(o.uf[6], o.uf[6]) : make_float2(o.uf[0], o.uf[0]);
+      const float2 cp = hi ? make_float2(o.uf[4], o.uf[4]) : make_float2(o.uf[2], o.uf[2]);
+      const bool all = tok && st.smask == 0;
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const float2 p = make_float2(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (!all && (!tok || (j & (int)st.smask) != (int)st.smask)) continue;
+#ifdef QS_HAVE_F32X2
+        const float2 r = __ffma2_rn(cs, make_float2(v[j].x, v[j].y), __fmul2_rn(cp, p));
+#else
+        const float2 r = make_float2(fmaf(cs.x, v[j].x, cp.x * p.x), fmaf(cs.x, v[j].y, cp.x * p.y));
+#endif
+        v[j] = cx<R>(r.x, r.y);
+      }
+      return;
+    }
+    // each lane keeps cs * own + cp * partner, with per-lane coefficients
+    const Cx<R> cs = hi ? u11 : u00, cp = hi ? u10 : u01;
+    if (st.smask == 0) {
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (tok) v[j] = cmac2(cs, v[j], cp, p);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (tok && (j & (int)st.smask) == (int)st.smask) v[j] = cmac2(cs, v[j], cp, p);
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    Cx<R> p = cx<R>(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+    if (!tok || (j & (int)st.smask) != (int)st.smask) continue;
+    Cx<R> a0 = hi ? p : v[j], a1 = hi ? v[j] : p;
+    switch (st.kind) {
+      case GK_HAD: {
+        const R s = uscal<R>(o);
+        v[j] = hi ? cx<R>((a0.x - a1.x) * s, (a0.y - a1.y) * s) : cx<R>((a0.x + a1.x) * s, (a0.y + a1.y) * s);
+        break;
+      }
+      case GK_ANTI:
+        v[j] = hi ? cmul_code(a0, u10, st.c1) : cmul_code(a1, u01, st.c0);
+        break;
+      case GK_DIAG:
+        v[j] = hi ? cmul_code(a1, u11, st.c1) : cmul_code(a0, u00, st.c0);
+        break;
+      default:
+        v[j] = hi ? cmac2(u10, a0, u11, a1) : cmac2(u00, a0, u01, a1);
+    }
+  }
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
+                                          int lane) {
+  if constexpr (sizeof(R) == 4) {
+    const float4* s4 = (const float4*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+      float4 x = s4[(base + woff + roff[jj]) >> 1];
+      v[2 * jj] = cx<float>(x.x, x.y);
+      v[2 * jj + 1] = cx<float>(x.z, x.w);
+    }
+  } else {
+    const double2* s2 = (const double2*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+      const uint64_t g = base + woff + roff[jj];
+      double2 x = s2[g], y = s2[g + 1];
+      v[2 * jj] = cx<double>(x.x, x.y);
+      v[2 * jj + 1] = cx<double>(y.x, y.y);
+    }
+  }
+}
+template <typename R, int RB>
+__device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
+                                           int lane) {
+  if constexpr (sizeof(R) == 4) {
+    float4* s4 = (float4*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj)
+      s4[(base + woff + roff[jj]) >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+  } else {
+    double2* s2 = (double2*)s;
+#pragma unroll
+    for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+      const uint64_t g = base + woff + roff[jj];
+      s2[g] = make_double2(v[2 * jj].x, v[2 * jj].y);
+      s2[g + 1] = make_double2(v[2 * jj + 1].x, v[2 * jj + 1].y);
+    }
+  }
+}
+
+// FEAT: which specialised complex64 paths the pass needs (bit 0: swaps, bit 1:
+// Hadamard-shaped); passes without them run a smaller kernel.
+constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_HAD: real-matrix path (packed FP32x2)
+
+// 16-byte global -> shared copies that bypass registers (LDGSTS), so the next
+// tile's loads are in flight while the current tile is computed and stored.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Each thread stages exactly the 16-byte chunks it will read back, so the
+// stage buffer needs no barrier: the thread's own wait_group orders it.
+template <typename R, int RB>
+__device__ __forceinline__ void stage_tile(const void* s, Cx<R>* st, uint64_t base, const uint64_t* roff, uint64_t woff,
+                                           const TMap& m, uint32_t tl) {
+#pragma unroll
+  for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
+    const uint64_t g = base + woff + roff[jj];
+    if constexpr (sizeof(R) == 4) {
+      cp_async16(((float4*)st) + (l >> 1), ((const float4*)s) + (g >> 1));
+    } else {
+      cp_async16(st + l, ((const double2*)s) + g);
+      cp_async16(st + l + 1, ((const double2*)s) + g + 1);
+    }
+  }
+  cp_async_commit();
+}
+template <typename R, int RB>
+__device__ __forceinline__ void unstage_tile(const Cx<R>* st, Cx<R>* v, const TMap& m, uint32_t tl) {
+#pragma unroll
+  for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
+    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
+    if constexpr (sizeof(R) == 4) {
+      const float4 x = ((const float4*)st)[l >> 1];
+      v[2 * jj] = cx<float>(x.x, x.y);
+      v[2 * jj + 1] = cx<float>(x.z, x.w);
+    } else {
+      v[2 * jj] = st[l];
+      v[2 * jj + 1] = st[l + 1];
+    }
+  }
+}
+
+// The body of a tile pass.  Prog gives the structure of op i (type, kind,
+// slot, control masks, fold flag): read from the parameters at run time
+// (ProgRT), or compile-time constants in a pass compiled at run time, where
+// the op loop unrolls completely and every branch on the structure folds.
+// The coefficients always come from P.ops[i].
+template <typename R, int RB, int FEAT, class Prog>
+__device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams2& P) {
+  extern __shared__ unsigned char smraw[];
+  constexpr int NR = 1 << RB;
+  // global offsets of the register part (pairs jj: slots 1..RB-1) at load / store
+  uint64_t* roff_in = (uint64_t*)smraw;
+  uint64_t* roff_out = roff_in + NR / 2;
+  // transpose buffer, 2^b elements; between the last transpose of a tile and
+  // the start of the next it stages the next tile
+  Cx<R>* xb = (Cx<R>*)(smraw + NR * sizeof(uint64_t));
+  Cx<R>* stg = xb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < NR / 2) {
+    roff_in[threadIdx.x] = goff(lidx<RB>(P.init, 2 * threadIdx.x, 0), P.gpos, P.b);
+    roff_out[threadIdx.x] = goff(lidx<RB>(P.fin, 2 * threadIdx.x, 0), P.gpos, P.b);
+  }
+  __syncthreads();
+  const uint64_t woff_in = goff(thread_part(P.init, lane, warp), P.gpos, P.b);
+  const uint64_t woff_out = goff(thread_part(P.fin, lane, warp), P.gpos, P.b);
+  const uint32_t tl_in = thread_part(P.init, lane, warp);
+  const uint64_t ntiles = 1ull << (P.N - P.b);
+  Cx<R> v[NR];
+  if (blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
+  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+    const uint64_t base = deposit_t(tau, P.out_mask);
+    cp_async_wait_all();
+    unstage_tile<R, RB>(stg, v, P.init, tl_in);
+    const uint64_t nxt = tau + gridDim.x;
+    if (P.last_xpose < 0 && nxt < ntiles)
+      stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
+    TMap cur = P.init;
+    uint32_t tl = thread_part(cur, lane, warp);
+    Cx<R> fac = cx<R>((R)1, (R)0);
+    int mapi = 0;
+    const int nops = Prog::kN >= 0 ? Prog::kN : P.nops;
+#pragma unroll
+    for (int i = 0; i < nops; ++i) {
+      const TOp& o = P.ops[i];
+      decltype(auto) st = Prog::s(P, i);
+      if (st.type == T_XPOSE) {
+        // write every register at its local index, read back under the new map
+#pragma unroll
+        for (int jj = 0; jj < NR / 2; ++jj) {
+          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
+          if constexpr (sizeof(R) == 4) {
+            ((float4*)xb)[l >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+          } else {
+            xb[l] = v[2 * jj];
+            xb[l + 1] = v[2 * jj + 1];
+          }
+        }
+        __syncthreads();
+        cur = P.maps[mapi++];
+        tl = thread_part(cur, lane, warp);
+#pragma unroll
+        for (int jj = 0; jj < NR / 2; ++jj) {
+          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
+          if constexpr (sizeof(R) == 4) {
+            float4 x = ((const float4*)xb)[l >> 1];
+            v[2 * jj] = cx<float>(x.x, x.y);
+            v[2 * jj + 1] = cx<float>(x.z, x.w);
+          } else {
+            v[2 * jj] = xb[l];
+            v[2 * jj + 1] = xb[l + 1];
+          }
+        }
+        __syncthreads();
+        if (i == P.last_xpose && nxt < ntiles)
+          stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
+        continue;
+      }
+      const bool gok = (base & st.gmask) == st.gmask;       // outer controls
+      const bool tok = (tl & st.tmask) == st.tmask;         // lane / warp controls
+      if (st.pad[0] != 0) {
+        // folded run of per-thread diagonals: multiply the factor, apply at the end
+        if (gok && tok) {
+          const bool one = (st.type == T_DIAG_THR) ? ((tl >> st.a) & 1) : ((base & st.gtbit) != 0);
+          if ((one ? st.c1 : st.c0) != 0) fac = cmul_code(fac, ucx<R>(o, one ? 3 : 0), 4);
+        }
+        if (st.pad[0] == 2) {
+          if (fac.x != (R)1 || fac.y != (R)0) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) v[j] = cmul_code(v[j], fac, 4);
+          }
+          fac = cx<R>((R)1, (R)0);
+        }
+        continue;
+      }
+      if (!gok) continue;
+      switch (st.type) {
+        case T_REG: {
+          if (!tok) break;
+          if constexpr (sizeof(R) == 4) {
+            // complex64: Hadamard-shaped or dense (exact for the unit entries
+            // of X, Y, CNOT, TOFFOLI)
+            // (a register-slot swap as renames makes the register allocation
+            // spill at 128 registers; swaps on register slots stay dense)
+            if ((FEAT & FEAT_HAD) && st.kind == GK_REAL) {
+              OpRealF f;
+              f.u00 = make_float2(o.uf[0], o.uf[0]); f.u01 = make_float2(o.uf[2], o.uf[2]);
+              f.u10 = make_float2(o.uf[4], o.uf[4]); f.u11 = make_float2(o.uf[6], o.uf[6]);
+              reg_op<R, RB>(v, st.a, st.smask, f);
+            } else {
+              OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
+              reg_op<R, RB>(v, st.a, st.smask, f);
+            }
+          } else {
+            // complex128: the FP64 pipe is the bound, so keep the cheaper forms
+            switch (st.kind) {
+              case GK_HAD: { OpHad<R> f; f.s = uscal<R>(o); reg_op<R, RB>(v, st.a, st.smask, f); break; }
+              case GK_ANTI: { OpAnti<R> f; f.f01 = ucx<R>(o, 1); f.f10 = ucx<R>(o, 2); f.c0 = st.c0; f.c1 = st.c1; reg_op<R, RB>(v, st.a, st.smask, f); break; }
+              default: {
+                OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
+                reg_op<R, RB>(v, st.a, st.smask, f);
+              }
+            }
+          }
+          break;
+        }
+        case T_LANE:
+          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0>(v, st, o, lane, tok);
+          break;
+        case T_DIAG_REG:
+        case T_DIAG_THR:
+        case T_DIAG_OUT: {
+          if (!tok) break;
+          const Cx<R> d0 = ucx<R>(o, 0), d1 = ucx<R>(o, 3);
+          if (st.type == T_DIAG_REG) {
+            if constexpr (sizeof(R) == 4) {
+              reg_diag_rt<R, RB>(v, st.a, st.smask, d0, d1, st.c0 == 0, st.c1 == 0);
+            } else {
+              const int sl = st.a;
+#pragma unroll
+              for (int j = 0; j < NR; ++j) {
+                if ((j & (int)st.smask) != (int)st.smask) continue;
+                const bool one = (j >> sl) & 1;
+                v[j] = one ? cmul_code(v[j], d1, st.c1) : cmul_code(v[j], d0, st.c0);
+              }
+            }
+          } else {
+            const bool one = (st.type == T_DIAG_THR) ? ((tl >> st.a) & 1) : ((base & st.gtbit) != 0);
+            const int code = one ? st.c1 : st.c0;
+            if (code == 0) break;
+            const Cx<R> d = one ? d1 : d0;
+            if (st.smask == 0) {
+#pragma unroll
+              for (int j = 0; j < NR; ++j) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
+            } else {
+#pragma unroll
+              for (int j = 0; j < NR; ++j)
+                if ((j & (int)st.smask) == (int)st.smask) v[j] = cmul_code(v[j], d, sizeof(R) == 4 ? 4 : code);
+            }
+          }
+          break;
+        }
+        default: break;
+      }
+    }
+    store_tile<R, RB>(s, v, base, roff_out, woff_out, lane);
+  }
+}
+
+
+// Op structure as compile-time constants (passes compiled at run time).
+struct OpS {
+  uint8_t type, kind, c0, c1, a;
+  uint8_t pad[3];
+  uint32_t smask, tmask;
+  uint64_t gmask, gtbit;
+};
+
+// Op structure read from the parameters (the interpreter).
+struct ProgRT {
+  static constexpr int kN = -1;
+  static __device__ __forceinline__ const TOp& s(const TileParams2& P, int i) { return P.ops[i]; }
+};
+
+}  // namespace qs_tile

@@ -81,6 +81,8 @@ _SIGS = {
     "modmul_table": (_I, [ctypes.c_uint64, ctypes.c_uint64, _I, ctypes.POINTER(ctypes.c_uint32)]),
     "shorbox_init": (_I, [_P, _I, ctypes.c_uint64, ctypes.c_uint64]),
     "circuit_run": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP]),
+    "circuit_compile": (_I, [_I, ctypes.POINTER(qs_gate), _I, _I, _IP]),
+    "tile_compiler_info": (_I, [_IP, ctypes.POINTER(ctypes.c_long)]),
     "circuit_run_timed": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP, ctypes.POINTER(ctypes.c_float), _I]),
     "gate_std": (_I, [ctypes.c_char_p, _IP, _I, _D, _I, ctypes.POINTER(qs_gate)]),
     "sim_norm": (_I, [_P, _D]),
@@ -164,6 +166,27 @@ def modmul_table(a, G, width):
     t = np.empty(1 << width, dtype=np.uint32)
     _check(_lib.modmul_table(int(a), int(G), int(width), t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
     return t
+
+
+def circuit_compile(N, gates, mode=2):
+    """Plan the complex64 tile passes of a circuit on N qubits and compile the
+    kernels that circuit_run in `mode` (2 or 3) would launch compiled (host
+    only).  Returns the number of passes planned."""
+    if isinstance(gates, tuple):
+        arr, n = gates
+    else:
+        arr, n = gate_array(gates)
+    npass = ctypes.c_int(0)
+    _check(_lib.circuit_compile(int(N), arr, n, int(mode), ctypes.byref(npass)))
+    return npass.value
+
+
+def tile_compiler_info():
+    """(NVRTC available, number of pass kernels compiled in this process)."""
+    a = ctypes.c_int(0)
+    c = ctypes.c_long(0)
+    _check(_lib.tile_compiler_info(ctypes.byref(a), ctypes.byref(c)))
+    return bool(a.value), int(c.value)
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,49 @@
+"""Host-side checks of the tile passes compiled at run time (no GPU work):
+the planner's passes of a circuit compile for sm_103a with NVRTC, compiled
+structures are cached, and bad arguments are rejected before compiling."""
+import pytest
+
+from paper_1805_04708_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_1805_04708_gb300 import build
+    build.build()
+    from paper_1805_04708_gb300 import qsim
+    if not qsim.tile_compiler_info()[0]:
+        pytest.skip("NVRTC cannot be loaded on this machine")
+    return qsim
+
+
+def test_circuit_compiles_and_is_cached(q):
+    recs = wl.random_mixed_circuit(16, 60, seed=3)
+    _, before = q.tile_compiler_info()
+    npass = q.circuit_compile(16, recs, mode=3)
+    _, after = q.tile_compiler_info()
+    assert npass >= 2
+    assert 1 <= after - before <= npass
+    # the same structures again: nothing new to compile
+    assert q.circuit_compile(16, recs, mode=3) == npass
+    assert q.tile_compiler_info()[1] == after
+
+
+def test_mode2_compiles_only_short_passes(q):
+    recs = wl.random_gate_circuit(22, 120, seed=5)
+    _, before = q.tile_compiler_info()
+    n2 = q.circuit_compile(22, recs, mode=2)
+    _, mid = q.tile_compiler_info()
+    n3 = q.circuit_compile(22, recs, mode=3)
+    _, after = q.tile_compiler_info()
+    assert n2 == n3
+    assert mid - before <= after - before <= n3
+
+
+def test_compile_rejects(q):
+    recs = [("H", (0,), ())]
+    with pytest.raises(q.QSError):
+        q.circuit_compile(16, recs, mode=1)
+    with pytest.raises(q.QSError):
+        q.circuit_compile(8, recs, mode=3)           # below the tile size
+    with pytest.raises(q.QSError):
+        q.circuit_compile(16, [("H", (16,), ())], mode=3)
