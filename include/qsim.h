@@ -178,12 +178,17 @@ qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
  * commutes with all of them (they share no qubit on which either acts
  * non-diagonally), so the circuit's product is unchanged.  The pass kernel:
  *   mode 1: the op interpreter compiled into the library;
- *   mode 2: for QS_C64 states, passes of at most 16 ops run a kernel compiled
- *           at run time for the pass's op structure (NVRTC, sm_103a; cached
- *           by structure, the first run of a new structure pays its compile
- *           time unless circuit_compile ran first); longer passes, and passes
- *           that fail to compile, use the interpreter;
- *   mode 3: the compiled kernel for every QS_C64 pass.
+ *   mode 2: for QS_C64 states, per pass structure (the pass's op types,
+ *           qubits and control masks; not its coefficients) the fastest of
+ *           the interpreter and three kernels compiled at run time for that
+ *           structure (NVRTC, sm_103a; without barriers, and with a CTA
+ *           barrier every 2 or every 8 ops).  The first four launches of a
+ *           structure try one candidate each, timed with CUDA events on the
+ *           handle's stream; later launches use the fastest.  Compiled
+ *           kernels are cached; a new structure pays its compile time unless
+ *           circuit_compile ran first; a variant that fails to compile is
+ *           never picked;
+ *   mode 3: the compiled kernel without barriers for every QS_C64 pass.
  * Modes 2 and 3 give QS_EUNSUPPORTED on a QS_C64 state when NVRTC cannot be
  * loaded; QS_C128 states use the interpreter in every tile mode.  Results
  * equal mode 0 up to floating-point rounding order.  gates: host array of n
@@ -192,8 +197,9 @@ qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
 qs_status circuit_run(qs_sim* sim, const qs_gate* gates, int n, int mode, int* n_passes);
 
 /* Plan the tile passes of a QS_C64 circuit on N qubits (13 <= N <= 63) and
- * compile the kernel of each new pass structure that circuit_run in `mode`
- * (2 or 3) would launch compiled (host only: no device call; NVRTC must be
+ * compile the kernels of each new pass structure that circuit_run in `mode`
+ * may launch (mode 2: its three compiled candidates; mode 3: the one kernel)
+ * on up to 16 host threads (host only: no device call; NVRTC must be
  * loadable, else QS_EUNSUPPORTED).  A later circuit_run of the same circuit
  * in that mode then launches without compiling.  n_passes (may be NULL)
  * receives the number of passes planned.  Gate validation as in

@@ -104,15 +104,16 @@ struct PassTimer {
 // Number of tile bits used by the tile passes for an encoding.
 int tile_bits(qs_encoding enc);
 // Plan a gate list into tile passes and launch them (the product of the
-// circuit is preserved).  jit: 0 the op interpreter; 1 kernels compiled at run
-// time for the short complex64 passes (the interpreter for the others, and
-// for a pass that fails to compile); 2 compiled kernels for every complex64
-// pass.  jit 1 and 2 give QS_EUNSUPPORTED on a complex64 state when NVRTC
-// cannot be loaded.
+// circuit is preserved).  jit: 0 the op interpreter; 1 per complex64 pass
+// structure the fastest of the interpreter and the kernels compiled at run
+// time (each timed once); 2 the compiled kernel (no barriers) for every
+// complex64 pass.  jit 1 and 2 give QS_EUNSUPPORTED on a complex64 state when
+// NVRTC cannot be loaded.
 qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer, int jit);
 // Plan the complex64 passes of an N-qubit circuit and compile each (host
-// only; the compiled kernels are cached for later launches): all passes when
-// all_passes, else those that mode 1 would run compiled.
+// only; the compiled kernels are cached for later launches): the kernel
+// circuit_run mode 3 launches (all_passes) or every compiled candidate of
+// mode 2.
 qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes);
 
 // ADAPT2 --------------------------------------------------------------------------

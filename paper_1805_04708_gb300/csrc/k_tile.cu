@@ -314,17 +314,13 @@ struct PassSink {
   qs_sim* s;            // null: compile only
   int N;
   qs_encoding enc;
-  int jit;              // 0: interpreter; 1: compiled kernels for passes of at
-                        // most TILE_JIT_MAX_OPS ops, else the interpreter;
-                        // 2: compiled kernels for every pass (complex64)
+  int jit;              // 0: interpreter; 1: per pass structure, the fastest of
+                        // the interpreter and the compiled variants (timed
+                        // online); 2: compiled, no barriers (complex64)
   PassTimer* timer;
   int emitted;
-  std::vector<TileParams2>* collect;   // compile only: the passes to compile
+  std::vector<JitJob>* collect;   // compile only: the kernels to compile
 };
-// A compiled pass is straight-line code whose length grows with its op count;
-// measured on GB300 at N = 30 it beats the interpreter up to about 16 ops and
-// loses beyond, where the unrolled code outgrows the instruction cache.
-constexpr int TILE_JIT_MAX_OPS = 16;
 
 static qs_status emit_pass(PassSink& k, const TileParams2& P);
 
@@ -421,7 +417,7 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
 }
 
 qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes) {
-  std::vector<TileParams2> passes;
+  std::vector<JitJob> passes;
   PassSink k = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes};
   QS_TRY(plan_tile_passes(k, gates, n));
   if (n_passes) *n_passes = k.emitted;
@@ -430,9 +426,20 @@ qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes,
 
 static qs_status launch_pass(PassSink& k, const TileParams2& P) {
   qs_sim* s = k.s;
-  // automatic choice: a pass that fails to compile runs on the interpreter
-  bool jit_ok = true;
-  if (k.jit == 1 && s->enc == QS_C64 && P.nops <= TILE_JIT_MAX_OPS) jit_ok = tile_jit_compile(P) == QS_OK;
+  // kernel of this launch: interpreter (cand 0) or a compiled variant
+  int cand = 0;
+  cudaEvent_t tune_end = nullptr;
+  if (s->enc == QS_C64 && k.jit == 2) cand = 1;
+  if (s->enc == QS_C64 && k.jit == 1) {
+    for (;;) {
+      QS_TRY(tile_tune_pick(s, P, &cand, &tune_end));
+      // a variant that fails to compile is never picked again
+      if (cand == 0 || tile_jit_compile(P, kTileCandSync[cand]) == QS_OK) break;
+      tile_tune_fail(P, cand);
+      if (tune_end) QS_CUDA(cudaEventRecord(tune_end, s->stream));
+      tune_end = nullptr;
+    }
+  }
   PassTimer* timer = k.timer;
   const bool timed = timer && timer->n < timer->max_ev;
   if (timed) QS_CUDA(cudaEventRecord(timer->ev[2 * timer->n], s->stream));
@@ -443,9 +450,9 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
     const size_t smem = ((size_t)16 << P.b) + 16 * sizeof(uint64_t);
     QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
-  } else if (k.jit == 2 || (k.jit == 1 && P.nops <= TILE_JIT_MAX_OPS && jit_ok)) {
+  } else if (cand > 0) {
     const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
-    QS_TRY(tile_jit_launch(s, P, grid, smem));
+    QS_TRY(tile_jit_launch(s, P, kTileCandSync[cand], grid, smem));
   } else {
     int feat = 0;
     for (int i = 0; i < P.nops; ++i) {
@@ -467,6 +474,7 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
     }
   }
   QS_LAUNCH_CHECK();
+  if (tune_end) QS_CUDA(cudaEventRecord(tune_end, s->stream));
   if (timed) {
     QS_CUDA(cudaEventRecord(timer->ev[2 * timer->n + 1], s->stream));
     timer->n++;
@@ -479,7 +487,11 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
 static qs_status emit_pass(PassSink& k, const TileParams2& P) {
   ++k.emitted;
   if (!k.s) {
-    if (k.jit == 2 || P.nops <= TILE_JIT_MAX_OPS) k.collect->push_back(P);
+    if (k.jit == 2) {
+      k.collect->push_back(JitJob{P, 0});
+    } else {
+      for (int c = 1; c < kTileCands; ++c) k.collect->push_back(JitJob{P, kTileCandSync[c]});
+    }
     return QS_OK;
   }
   return launch_pass(k, P);

@@ -378,6 +378,10 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
     for (int i = 0; i < nops; ++i) {
       const TOp& o = P.ops[i];
       decltype(auto) st = Prog::s(P, i);
+      // a compiled long pass may keep the CTA's warps within a few ops of each
+      // other, so that they share the instruction lines they fetch
+      if constexpr (Prog::kSync > 0)
+        if (i > 0 && i % Prog::kSync == 0) __syncthreads();
       if (st.type == T_XPOSE) {
         // write every register at its local index, read back under the new map
 #pragma unroll
@@ -513,6 +517,7 @@ struct OpS {
 // Op structure read from the parameters (the interpreter).
 struct ProgRT {
   static constexpr int kN = -1;
+  static constexpr int kSync = 0;
   static __device__ __forceinline__ const TOp& s(const TileParams2& P, int i) { return P.ops[i]; }
 };
 

@@ -8,6 +8,13 @@
 // (tile_core.cuh) unrolls completely and every branch on the structure folds
 // away, leaving straight-line arithmetic.  The coefficients stay in the
 // parameters, so passes of the same structure share one compiled kernel.
+// A variant adds a CTA barrier every few ops (long passes outgrow the
+// instruction cache; warps kept together share the lines they fetch).
+//
+// circuit_run mode 2 picks, per pass structure, among the interpreter and
+// three compiled variants by timing each once with CUDA events (a pass's
+// duration does not depend on the amplitudes, only on its structure) and
+// then keeps the fastest.
 //
 // NVRTC is loaded with dlopen on first use; without it the compiled path
 // reports itself unavailable and the interpreter runs the passes.
@@ -77,11 +84,13 @@ std::unordered_map<std::string, Entry>& cache() {
 }
 long g_compiles = 0;
 
-// The structure of the pass as a compile-time program.
-std::string program_of(const TileParams2& P) {
+// The structure of the pass as a compile-time program (sync: barrier every
+// `sync` ops, 0 for none).
+std::string program_of(const TileParams2& P, int sync) {
   std::string s;
   char buf[256];
-  snprintf(buf, sizeof buf, "struct ProgJ {\n  static constexpr int kN = %d;\n", P.nops);
+  snprintf(buf, sizeof buf, "struct ProgJ {\n  static constexpr int kN = %d;\n  static constexpr int kSync = %d;\n",
+           P.nops, sync);
   s += buf;
   s += "  static __device__ __forceinline__ OpS s(const TileParams2&, int i) {\n    switch (i) {\n";
   for (int i = 0; i < P.nops; ++i) {
@@ -148,8 +157,8 @@ qs_status compile_prog(const std::string& prog, Entry& e) {
 // The cache entry of a pass's structure, compiled if new.  The compile runs
 // outside the lock, so several passes can compile at once; if two threads
 // compile the same structure, the first result is kept.
-qs_status entry_of(const TileParams2& P, Entry** out) {
-  const std::string prog = program_of(P);
+qs_status entry_of(const TileParams2& P, int sync, Entry** out) {
+  const std::string prog = program_of(P, sync);
   {
     std::lock_guard<std::mutex> g(g_mu);
     auto it = cache().find(prog);
@@ -175,12 +184,12 @@ long tile_jit_compiles() {
   return g_compiles;
 }
 
-qs_status tile_jit_compile(const TileParams2& P) {
+qs_status tile_jit_compile(const TileParams2& P, int sync) {
   Entry* e;
-  return entry_of(P, &e);
+  return entry_of(P, sync, &e);
 }
 
-qs_status tile_jit_compile_all(const std::vector<TileParams2>& passes) {
+qs_status tile_jit_compile_all(const std::vector<JitJob>& passes) {
   const size_t n = passes.size();
   unsigned nt = std::thread::hardware_concurrency();
   if (nt == 0) nt = 4;
@@ -190,7 +199,7 @@ qs_status tile_jit_compile_all(const std::vector<TileParams2>& passes) {
   std::atomic<int> status((int)QS_OK);
   auto work = [&] {
     for (size_t i; (i = next.fetch_add(1)) < n;) {
-      const qs_status st = tile_jit_compile(passes[i]);
+      const qs_status st = tile_jit_compile(passes[i].P, passes[i].sync);
       if (st != QS_OK) status.store((int)st);
     }
   };
@@ -201,9 +210,9 @@ qs_status tile_jit_compile_all(const std::vector<TileParams2>& passes) {
   return (qs_status)status.load();
 }
 
-qs_status tile_jit_launch(qs_sim* s, const TileParams2& P, unsigned grid, size_t smem) {
+qs_status tile_jit_launch(qs_sim* s, const TileParams2& P, int sync, unsigned grid, size_t smem) {
   Entry* e;
-  QS_TRY(entry_of(P, &e));
+  QS_TRY(entry_of(P, sync, &e));
   cudaKernel_t k;
   {
     std::lock_guard<std::mutex> g(g_mu);
@@ -221,4 +230,70 @@ qs_status tile_jit_launch(qs_sim* s, const TileParams2& P, unsigned grid, size_t
   void* args[] = {&state, (void*)&P};
   QS_CUDA(cudaLaunchKernel((const void*)k, dim3(grid), dim3(TPB), args, smem, s->stream));
   return QS_OK;
+}
+
+// ---- online choice of the pass kernel (circuit_run mode 2) --------------------
+namespace {
+struct Tune {
+  int next = 0, best = -1;
+  bool launched[kTileCands] = {}, done[kTileCands] = {};
+  float ms[kTileCands] = {};
+  cudaEvent_t ev[kTileCands][2] = {};
+};
+std::unordered_map<std::string, Tune>& tunes() {
+  static std::unordered_map<std::string, Tune> t;
+  return t;
+}
+}  // namespace
+
+const int kTileCandSync[kTileCands] = {0, 0, 2, 8};
+
+qs_status tile_tune_pick(qs_sim* s, const TileParams2& P, int* cand, cudaEvent_t* end_ev) {
+  *end_ev = nullptr;
+  std::lock_guard<std::mutex> g(g_mu);
+  Tune& t = tunes()[program_of(P, -1)];
+  if (t.best < 0) {
+    bool all = true;
+    for (int c = 0; c < kTileCands; ++c) {
+      if (t.launched[c] && !t.done[c] && cudaEventQuery(t.ev[c][1]) == cudaSuccess) {
+        QS_CUDA(cudaEventElapsedTime(&t.ms[c], t.ev[c][0], t.ev[c][1]));
+        t.done[c] = true;
+      }
+      all = all && t.done[c];
+    }
+    if (all) {
+      t.best = 0;
+      for (int c = 1; c < kTileCands; ++c)
+        if (t.ms[c] < t.ms[t.best]) t.best = c;
+    }
+  }
+  if (t.best >= 0) {
+    *cand = t.best;
+    return QS_OK;
+  }
+  if (t.next < kTileCands) {
+    const int c = t.next++;
+    if (!t.ev[c][0]) {
+      QS_CUDA(cudaEventCreate(&t.ev[c][0]));
+      QS_CUDA(cudaEventCreate(&t.ev[c][1]));
+    }
+    QS_CUDA(cudaEventRecord(t.ev[c][0], s->stream));
+    t.launched[c] = true;
+    *cand = c;
+    *end_ev = t.ev[c][1];
+    return QS_OK;
+  }
+  // every candidate launched, some still running: the fastest measured so far
+  int best = 0;
+  for (int c = 1; c < kTileCands; ++c)
+    if (t.done[c] && (!t.done[best] || t.ms[c] < t.ms[best])) best = c;
+  *cand = best;
+  return QS_OK;
+}
+
+void tile_tune_fail(const TileParams2& P, int cand) {
+  std::lock_guard<std::mutex> g(g_mu);
+  Tune& t = tunes()[program_of(P, -1)];
+  t.done[cand] = true;
+  t.ms[cand] = 3.0e38f;
 }

@@ -28,15 +28,18 @@ def test_circuit_compiles_and_is_cached(q):
     assert q.tile_compiler_info()[1] == after
 
 
-def test_mode2_compiles_only_short_passes(q):
+def test_mode2_compiles_every_candidate(q):
+    # mode 3 compiles one kernel per structure; mode 2 adds the two variants
+    # with CTA barriers (the variant without barriers is shared)
     recs = wl.random_gate_circuit(22, 120, seed=5)
-    _, before = q.tile_compiler_info()
-    n2 = q.circuit_compile(22, recs, mode=2)
-    _, mid = q.tile_compiler_info()
+    _, c0 = q.tile_compiler_info()
     n3 = q.circuit_compile(22, recs, mode=3)
-    _, after = q.tile_compiler_info()
+    _, c1 = q.tile_compiler_info()
+    n2 = q.circuit_compile(22, recs, mode=2)
+    _, c2 = q.tile_compiler_info()
     assert n2 == n3
-    assert mid - before <= after - before <= n3
+    assert 1 <= c1 - c0 <= n3
+    assert c2 - c1 == 2 * (c1 - c0)
 
 
 def test_compile_rejects(q):
