@@ -42,10 +42,11 @@ UNIT = "updates/s"
 # algorithmic bytes of one tile pass: read + write of the whole state
 # (2 * 2^N * 8 B for complex64)
 # DRAM bytes per tile-pass launch at N = 30, from one ncu capture of the
-# N = 26 random-gate circuit in circuit_run mode 2 (both pass kernels) scaled
+# N = 26 random-gate circuit in circuit_run mode 2 (after its kernel choice;
+# interpreter and compiled passes) scaled
 # by the 16x units (profiles/tile_pass_c64_n26_traffic.md); None when a pass
 # kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = 1.6255e10
+TILE_TRAFFIC_PER_PASS = 1.6275e10
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
