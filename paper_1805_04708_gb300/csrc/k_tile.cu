@@ -286,6 +286,59 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
     }
     i = (j > i) ? j : i + 1;
   }
+  // runs of register-slot diagonals without lane, warp or outer controls
+  // become one multiplication by a table of per-register factors, the
+  // products formed in FP64 on the host (a control on a register slot gives
+  // factor 1 to the registers where it is 0)
+  {
+    const int NRj = 1 << RB;
+    int m = 0, ntab = 0;
+    auto tabbable = [&](int k) {
+      const TOp& o = P->ops[k];
+      return o.type == T_DIAG_REG && o.tmask == 0 && o.gmask == 0;
+    };
+    for (int i = 0; i < nops;) {
+      int j = i;
+      while (j < nops && tabbable(j)) ++j;
+      if (j - i >= 2 && ntab < MAX_TABS) {
+        double tr[32], ti[32];
+        for (int r = 0; r < NRj; ++r) { tr[r] = 1.0; ti[r] = 0.0; }
+        for (int k = i; k < j; ++k) {
+          const TOp& o = P->ops[k];
+          for (int r = 0; r < NRj; ++r) {
+            if ((r & (int)o.smask) != (int)o.smask) continue;
+            const int bit = (r >> o.a) & 1;
+            const double dr = o.ud[bit ? 6 : 0], di = o.ud[bit ? 7 : 1];
+            const double xr = tr[r] * dr - ti[r] * di, xi = tr[r] * di + ti[r] * dr;
+            tr[r] = xr; ti[r] = xi;
+          }
+        }
+        for (int r = 0; r < NRj; ++r) {
+          if (real_kinds) {
+            const float fr = (float)tr[r], fi = (float)ti[r];
+            uint32_t br, bi;
+            memcpy(&br, &fr, 4); memcpy(&bi, &fi, 4);
+            P->tab[ntab][r] = (uint64_t)br | ((uint64_t)bi << 32);
+          } else {
+            memcpy(&P->tab[ntab][2 * r], &tr[r], 8);
+            memcpy(&P->tab[ntab][2 * r + 1], &ti[r], 8);
+          }
+        }
+        TOp t;
+        memset(&t, 0, sizeof t);
+        t.type = T_DIAG_TAB;
+        t.a = (uint8_t)ntab++;
+        P->ops[m++] = t;
+        i = j;
+      } else if (j > i) {
+        for (int k = i; k < j; ++k) P->ops[m++] = P->ops[k];
+        i = j;
+      } else {
+        P->ops[m++] = P->ops[i++];
+      }
+    }
+    nops = m;
+  }
   // runs of per-thread diagonals (target on a lane / warp bit or outside the
   // tile, no register-slot control) fold into one factor per thread
   for (int i = 0; i < nops;) {

@@ -37,7 +37,9 @@ constexpr int WARP_BITS = 3;
 constexpr int MAX_TOPS = 96;
 constexpr int LOW_BITS = 4;   // index bits always in the tile (16-amplitude runs)
 
-enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5 };
+enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5,
+                         T_DIAG_TAB = 6 };
+constexpr int MAX_TABS = 8;   // per-register factor tables of a pass
 
 struct TOp {
   uint8_t type, kind, c0, c1;
@@ -64,6 +66,9 @@ struct TileParams2 {
   int last_xpose;      // index of the last transpose op, -1 if none
   TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
   TMap maps[16];
+  // T_DIAG_TAB: the factor of register j, complex64 (re, im) float bits in
+  // tab[t][j]; complex128 re, im double bits in tab[t][2j], tab[t][2j+1]
+  uint64_t tab[MAX_TABS][32];
 };
 
 __device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
@@ -465,6 +470,22 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
         case T_LANE:
           lane_op<R, RB, (FEAT & FEAT_SWAP) != 0>(v, st, o, lane, tok);
           break;
+        case T_DIAG_TAB: {
+          // a run of register-slot diagonals multiplied out on the host
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            Cx<R> f;
+            if constexpr (sizeof(R) == 4) {
+              const uint64_t w = P.tab[st.a][j];
+              f = cx<R>(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)));
+            } else {
+              f = cx<R>(__longlong_as_double((long long)P.tab[st.a][2 * j]),
+                        __longlong_as_double((long long)P.tab[st.a][2 * j + 1]));
+            }
+            v[j] = cmul_code(v[j], f, 4);
+          }
+          break;
+        }
         case T_DIAG_REG:
         case T_DIAG_THR:
         case T_DIAG_OUT: {
