@@ -97,6 +97,22 @@ struct OpRealF {
     a1 = cx<float>(B1.x, B1.y);
   }
 };
+// Unscaled Hadamard butterfly on complex64 pairs: one packed instruction per
+// output (the pass applies the dropped scale factors elsewhere, once).
+struct OpBflyF {
+  __device__ __forceinline__ void pair(Cx<float>& a0, Cx<float>& a1) const {
+    const float2 A0 = make_float2(a0.x, a0.y), A1 = make_float2(a1.x, a1.y);
+#ifdef QS_HAVE_F32X2
+    const float2 B0 = __fadd2_rn(A0, A1);
+    const float2 B1 = __ffma2_rn(make_float2(-1.f, -1.f), A1, A0);
+#else
+    const float2 B0 = make_float2(A0.x + A1.x, A0.y + A1.y);
+    const float2 B1 = make_float2(A0.x - A1.x, A0.y - A1.y);
+#endif
+    a0 = cx<float>(B0.x, B0.y);
+    a1 = cx<float>(B1.x, B1.y);
+  }
+};
 template <typename R> struct OpMul {
   Cx<R> f; int c;
   __device__ __forceinline__ void one(Cx<R>& a) const { a = cmul_code(a, f, c); }

@@ -8,5 +8,6 @@ enum GateKind : int {
   GK_DIAG = 2,    // diag(d0, d1)
   GK_ANTI = 3,    // [[0, f01], [f10, 0]]
   GK_IDENT = 4,   // identity (no-op)
-  GK_REAL = 5     // real dense u (tile passes of complex64 states only)
+  GK_REAL = 5,    // real dense u (tile passes of complex64 states only)
+  GK_BFLY = 6     // (a0 + a1, a0 - a1): a Hadamard without its scale (idem)
 };

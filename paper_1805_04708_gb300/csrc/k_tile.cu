@@ -290,9 +290,11 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
   // become one multiplication by a table of per-register factors, the
   // products formed in FP64 on the host (a control on a register slot gives
   // factor 1 to the registers where it is 0)
+  const int NRj = 1 << RB;
+  static thread_local double tabd[MAX_TABS][32][2];
+  int ntab = 0;
   {
-    const int NRj = 1 << RB;
-    int m = 0, ntab = 0;
+    int m = 0;
     auto tabbable = [&](int k) {
       const TOp& o = P->ops[k];
       return o.type == T_DIAG_REG && o.tmask == 0 && o.gmask == 0;
@@ -313,17 +315,7 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
             tr[r] = xr; ti[r] = xi;
           }
         }
-        for (int r = 0; r < NRj; ++r) {
-          if (real_kinds) {
-            const float fr = (float)tr[r], fi = (float)ti[r];
-            uint32_t br, bi;
-            memcpy(&br, &fr, 4); memcpy(&bi, &fi, 4);
-            P->tab[ntab][r] = (uint64_t)br | ((uint64_t)bi << 32);
-          } else {
-            memcpy(&P->tab[ntab][2 * r], &tr[r], 8);
-            memcpy(&P->tab[ntab][2 * r + 1], &ti[r], 8);
-          }
-        }
+        for (int r = 0; r < NRj; ++r) { tabd[ntab][r][0] = tr[r]; tabd[ntab][r][1] = ti[r]; }
         TOp t;
         memset(&t, 0, sizeof t);
         t.type = T_DIAG_TAB;
@@ -339,6 +331,72 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
     }
     nops = m;
   }
+  // complex64: uncontrolled ops of the form s [[1, 1], [1, -1]] (Hadamards)
+  // become unscaled butterflies (coefficients [[1, 1], [1, -1]]); the product
+  // of their scales, a scalar that commutes with every op, goes into the
+  // first factor table of the pass, else into an uncontrolled real or dense
+  // op, else stays with one of the Hadamards
+  if (real_kinds) {
+    auto unc = [&](const TOp& o) {
+      return (o.type == T_REG || o.type == T_LANE) && o.smask == 0 && o.tmask == 0 && o.gmask == 0;
+    };
+    auto had_scale = [&](const TOp& o) -> double {
+      const double* u = o.ud;
+      if (o.kind != GK_REAL || u[1] != 0.0 || u[3] != 0.0 || u[5] != 0.0 || u[7] != 0.0) return 0.0;
+      if (!(u[0] > 0.0) || u[2] != u[0] || u[4] != u[0] || u[6] != -u[0]) return 0.0;
+      return u[0];
+    };
+    int nh = 0, first_h = -1, carrier = -1;
+    for (int i = 0; i < nops; ++i) {
+      const TOp& o = P->ops[i];
+      if (!unc(o)) continue;
+      if (had_scale(o) > 0.0) {
+        if (first_h < 0) first_h = i;
+        ++nh;
+      } else if (carrier < 0 && (o.kind == GK_REAL || o.kind == GK_DENSE)) {
+        carrier = i;
+      }
+    }
+    if (nh >= 2 || (nh == 1 && (ntab > 0 || carrier >= 0))) {
+      double scale = 1.0;
+      const double bf[8] = {1, 0, 1, 0, 1, 0, -1, 0};
+      for (int i = 0; i < nops; ++i) {
+        TOp& o = P->ops[i];
+        if (!unc(o)) continue;
+        const double sc = had_scale(o);
+        if (sc > 0.0) {
+          scale *= sc;
+          o.kind = GK_BFLY;
+          fill_u(o, bf);
+        }
+      }
+      if (ntab > 0) {
+        for (int r = 0; r < NRj; ++r) { tabd[0][r][0] *= scale; tabd[0][r][1] *= scale; }
+      } else {
+        if (carrier < 0) {   // one of the Hadamards keeps the whole scale
+          carrier = first_h;
+          P->ops[carrier].kind = GK_REAL;
+        }
+        TOp& c = P->ops[carrier];
+        double u[8];
+        for (int k = 0; k < 8; ++k) u[k] = c.ud[k] * scale;
+        fill_u(c, u);
+      }
+    }
+  }
+  // the factor tables in the state's precision
+  for (int t = 0; t < ntab; ++t)
+    for (int r = 0; r < NRj; ++r) {
+      if (real_kinds) {
+        const float fr = (float)tabd[t][r][0], fi = (float)tabd[t][r][1];
+        uint32_t br, bi;
+        memcpy(&br, &fr, 4); memcpy(&bi, &fi, 4);
+        P->tab[t][r] = (uint64_t)br | ((uint64_t)bi << 32);
+      } else {
+        memcpy(&P->tab[t][2 * r], &tabd[t][r][0], 8);
+        memcpy(&P->tab[t][2 * r + 1], &tabd[t][r][1], 8);
+      }
+    }
   // runs of per-thread diagonals (target on a lane / warp bit or outside the
   // tile, no register-slot control) fold into one factor per thread
   for (int i = 0; i < nops;) {
@@ -511,7 +569,7 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
     for (int i = 0; i < P.nops; ++i) {
       const TOp& o = P.ops[i];
       if (o.type == T_LANE && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) feat |= FEAT_SWAP;
-      if ((o.type == T_REG || o.type == T_LANE) && o.kind == GK_REAL) feat |= FEAT_HAD;
+      if ((o.type == T_REG || o.type == T_LANE) && (o.kind == GK_REAL || o.kind == GK_BFLY)) feat |= FEAT_HAD;
     }
     const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
     auto go = [&](auto kern) -> qs_status {

@@ -178,7 +178,10 @@ template <> __device__ __forceinline__ float shx<float>(float x, int m) { return
 template <> __device__ __forceinline__ double shx<double>(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
 
 // lane-bit op: partner values by shuffle, each lane keeps its own output
-template <typename R, int RB, bool SWAP, class OS>
+// CT: the op's structure is a compile-time constant (compiled passes), which
+// enables the butterfly form of GK_BFLY; the interpreter runs GK_BFLY as the
+// real matrix [[1, 1], [1, -1]] that its coefficients hold.
+template <typename R, int RB, bool SWAP, bool CT, class OS>
 __device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, int lane, bool tok) {
   const int m = 1 << st.a;
   const bool hi = (lane >> st.a) & 1;
@@ -193,7 +196,23 @@ __device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, in
       }
       return;
     }
-    if (st.kind == GK_REAL) {
+    if (CT && st.kind == GK_BFLY) {
+      // butterfly: own + partner (low lane), partner - own (high lane)
+      const float2 sg = hi ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+#pragma unroll
+      for (int j = 0; j < (1 << RB); ++j) {
+        const float2 p = make_float2(shx<R>(v[j].x, m), shx<R>(v[j].y, m));
+        if (!tok || (j & (int)st.smask) != (int)st.smask) continue;
+#ifdef QS_HAVE_F32X2
+        const float2 r = __ffma2_rn(sg, make_float2(v[j].x, v[j].y), p);
+#else
+        const float2 r = make_float2(fmaf(sg.x, v[j].x, p.x), fmaf(sg.x, v[j].y, p.y));
+#endif
+        v[j] = cx<R>(r.x, r.y);
+      }
+      return;
+    }
+    if (st.kind == GK_REAL || st.kind == GK_BFLY) {
       // real coefficients: packed FP32x2 on (re, im)
       const float2 cs = hi ? make_float2(o.uf[6], o.uf[6]) : make_float2(o.uf[0], o.uf[0]);
       const float2 cp = hi ? make_float2(o.uf[4], o.uf[4]) : make_float2(o.uf[2], o.uf[2]);
@@ -445,7 +464,10 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
             // of X, Y, CNOT, TOFFOLI)
             // (a register-slot swap as renames makes the register allocation
             // spill at 128 registers; swaps on register slots stay dense)
-            if ((FEAT & FEAT_HAD) && st.kind == GK_REAL) {
+            if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
+              OpBflyF f;
+              reg_op<R, RB>(v, st.a, st.smask, f);
+            } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY)) {
               OpRealF f;
               f.u00 = make_float2(o.uf[0], o.uf[0]); f.u01 = make_float2(o.uf[2], o.uf[2]);
               f.u10 = make_float2(o.uf[4], o.uf[4]); f.u11 = make_float2(o.uf[6], o.uf[6]);
@@ -468,7 +490,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
           break;
         }
         case T_LANE:
-          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0>(v, st, o, lane, tok);
+          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0, (Prog::kN >= 0)>(v, st, o, lane, tok);
           break;
         case T_DIAG_TAB: {
           // a run of register-slot diagonals multiplied out on the host
