@@ -519,6 +519,8 @@ def run_profile_case(args):
                kernel candidate, four times), then <Qx,Qy,Qz> (complex64)
       fused  : a dense k-qubit gate on qubits 0..k-1, applied three times
                (complex64; the tcgen05 kernel for k >= 3)
+      expect : BEGIN MEASUREMENT (<Qx,Qy,Qz> of every qubit) twice on the
+               state after the random-gate circuit (complex64)
       ops    : four single-pass circuits of one op class each (complex64):
                an empty pass, 20 H on register-slot qubits, 21 H on lane
                qubits, 20 U3 on register-slot qubits"""
@@ -534,7 +536,11 @@ def run_profile_case(args):
             for _ in range(4):
                 s.reset()
                 s.circuit_run(workload_records(N), mode=2)
-        if args.profile_case == "ops":
+        if args.profile_case == "expect":
+            s.circuit_run(workload_records(N), mode=1)
+            s.expect_xyz()
+            s.expect_xyz()
+        elif args.profile_case == "ops":
             top = N - 1
             slots = [0, top - 6, top - 5, top - 4, top - 3]      # register slots
             lanes = [1, 2, 3]                                    # lane qubits
@@ -570,7 +576,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["tile", "fused", "ops"], default=None,
+    ap.add_argument("--profile-case", choices=["tile", "fused", "ops", "expect"], default=None,
                     help="run a small workload for a profiler and exit")
     ap.add_argument("--qubits", type=int, default=26)
     ap.add_argument("--k", type=int, default=5)
