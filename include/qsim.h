@@ -104,8 +104,19 @@ qs_status sim_destroy(qs_sim* sim);
  * in bytes. */
 qs_status sim_info(const qs_sim* sim, int* N, int* enc, void** dev_ptr, size_t* bytes);
 
-/* Reset to |0..0> (a_0 = 1). */
+/* Reset to |0..0> (a_0 = 1).  With lazy reset (the default for sim_create,
+ * see sim_set_lazy_reset) nothing is written yet: the first tile pass of a
+ * following circuit_run makes its tiles from |0..0> instead of reading them,
+ * and every other call that reads or writes the amplitudes (including
+ * sim_info asking for the device pointer) writes |0..0> first. */
 qs_status sim_reset(qs_sim* sim);
+
+/* Turn lazy reset on or off (on: nonzero).  Default on for sim_create, off
+ * for sim_create_in, whose buffer its owner may read without a call of this
+ * library; a caller that only reaches the amplitudes through this library
+ * may turn it on.  Turning it off writes a pending |0..0>.  The paper has no
+ * counterpart. */
+qs_status sim_set_lazy_reset(qs_sim* sim, int on);
 
 /* ---- gates (Sec. 2, Eq. (NUM2); Appendix A) ------------------------------ */
 /* Single-qubit gate: for every basis index i with bit `target` = 0,

@@ -59,15 +59,33 @@ static qs_status init_handle(qs_sim* s, int N, qs_encoding enc, void* stream) {
   s->hbuf = nullptr;
   s->hbuf_bytes = 0;
   s->fused_engine = QS_FUSED_AUTO;
+  s->zero_pending = false;
+  s->lazy_reset = false;
   QS_CUDA(cudaGetDevice(&s->device));
   QS_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
   if (enc == QS_ADAPT2) QS_CUDA(cudaMalloc(&s->a2dev, sizeof(A2Dev)));
   return QS_OK;
 }
 
+// A lazy dense state is reset without a write: |0..0> is left to the first
+// tile pass (which makes the tiles instead of loading them) or to
+// materialize_state.  Other states are written at once (a caller's buffer
+// may be read by its owner directly).
 static qs_status do_reset(qs_sim* s) {
   if (s->enc == QS_ADAPT2) return a2_reset(s);
+  if (s->lazy_reset) {
+    s->zero_pending = true;
+    return QS_OK;
+  }
+  s->zero_pending = false;
   return launch_reset(s);
+}
+
+qs_status materialize_state(qs_sim* s) {
+  if (!s->zero_pending) return QS_OK;
+  QS_TRY(launch_reset(s));
+  s->zero_pending = false;
+  return QS_OK;
 }
 
 extern "C" qs_status sim_create(int N, qs_encoding enc, void* cuda_stream, qs_sim** out) {
@@ -97,6 +115,7 @@ extern "C" qs_status sim_create(int N, qs_encoding enc, void* cuda_stream, qs_si
   }
   s->bytes = bytes;
   s->owns = true;
+  s->lazy_reset = true;
   st = do_reset(s);
   if (st != QS_OK) { cudaFree(s->state); if (s->a2dev) cudaFree(s->a2dev); delete s; return st; }
   *out = s;
@@ -144,6 +163,8 @@ extern "C" qs_status sim_destroy(qs_sim* s) {
 
 extern "C" qs_status sim_info(const qs_sim* s, int* N, int* enc, void** dev_ptr, size_t* bytes) {
   QS_TRY(check_sim(s));
+  // the caller may read the amplitudes through the pointer
+  if (dev_ptr) QS_TRY(materialize_state(const_cast<qs_sim*>(s)));
   if (N) *N = s->N;
   if (enc) *enc = (int)s->enc;
   if (dev_ptr) *dev_ptr = s->state;
@@ -154,6 +175,13 @@ extern "C" qs_status sim_info(const qs_sim* s, int* N, int* enc, void** dev_ptr,
 extern "C" qs_status sim_reset(qs_sim* s) {
   QS_TRY(check_sim(s));
   return do_reset(s);
+}
+
+extern "C" qs_status sim_set_lazy_reset(qs_sim* s, int on) {
+  QS_TRY(check_sim(s));
+  if (!on) QS_TRY(materialize_state(s));
+  s->lazy_reset = on != 0;
+  return QS_OK;
 }
 
 extern "C" qs_status sim_sync(qs_sim* s) {
@@ -176,6 +204,7 @@ static qs_status check_u2(const double* U) {
 
 static qs_status apply_u2_checked(qs_sim* s, const int* controls, int nc, int target, const double* U) {
   if (s->enc == QS_ADAPT2) return a2_apply_u2(s, controls, nc, target, U);
+  QS_TRY(materialize_state(s));
   return launch_u2(s, controls, nc, target, U);
 }
 
@@ -213,6 +242,7 @@ extern "C" qs_status apply_fused(qs_sim* s, const int* qubits, int k, const doub
     return QS_ENOTUNITARY;
   }
   if (s->enc == QS_ADAPT2) { qs_set_error("apply_fused: not available for QS_ADAPT2"); return QS_EUNSUPPORTED; }
+  QS_TRY(materialize_state(s));
   return launch_fused_dense(s, qubits, k, U);
 }
 
@@ -258,6 +288,7 @@ extern "C" qs_status apply_permutation(qs_sim* s, const int* controls, int nc, i
     seen[table[i]] = 1;
   }
   free(seen);
+  QS_TRY(materialize_state(s));
   return launch_permutation(s, controls, nc, reg_lo, reg_w, table);
 }
 
@@ -266,6 +297,7 @@ extern "C" qs_status shorbox_init(qs_sim* s, int nx, uint64_t G, uint64_t y) {
   CHECK_ARG(nx >= 1 && nx < s->N, "shorbox_init: nx = %d not in 1..N-1", nx);
   CHECK_ARG(G >= 2 && G <= (1ull << (s->N - nx)) && G < (1ull << 32), "shorbox_init: G out of range");
   CHECK_ARG(y >= 1 && y < G, "shorbox_init: y out of range");
+  s->zero_pending = false;   // every amplitude is written
   return (s->enc == QS_ADAPT2) ? a2_shorbox(s, nx, G, y) : launch_shorbox(s, nx, G, y);
 }
 
@@ -378,12 +410,14 @@ extern "C" qs_status circuit_run_timed(qs_sim* s, const qs_gate* gates, int n, i
 extern "C" qs_status sim_norm(qs_sim* s, double* out) {
   QS_TRY(check_sim(s));
   CHECK_ARG(out != nullptr, "sim_norm: null out");
+  QS_TRY(materialize_state(s));
   return (s->enc == QS_ADAPT2) ? a2_norm(s, out) : launch_norm(s, out);
 }
 
 extern "C" qs_status expect_xyz(qs_sim* s, double* qx, double* qy, double* qz) {
   QS_TRY(check_sim(s));
   CHECK_ARG(qx && qy && qz, "expect_xyz: null output");
+  QS_TRY(materialize_state(s));
   return launch_expect(s, qx, qy, qz);
 }
 
@@ -392,6 +426,7 @@ extern "C" qs_status measure_probs(qs_sim* s, const int* qubits, int nq, double*
   CHECK_ARG(nq >= 1 && nq <= 24 && nq <= s->N, "measure_probs: nq = %d not in 1..min(24, N)", nq);
   CHECK_ARG(out != nullptr, "measure_probs: null out");
   QS_TRY(check_qubits(s, qubits, nq, "measure_probs"));
+  QS_TRY(materialize_state(s));
   return launch_marginal(s, qubits, nq, out);
 }
 
@@ -399,6 +434,7 @@ extern "C" qs_status measure_probs(qs_sim* s, const int* qubits, int nq, double*
 extern "C" qs_status sim_copy_out(qs_sim* s, void* host, size_t bytes, double* r0r1) {
   QS_TRY(check_sim(s));
   CHECK_ARG(host != nullptr && bytes == s->bytes, "sim_copy_out: need %zu bytes", s->bytes);
+  QS_TRY(materialize_state(s));
   QS_CUDA(cudaMemcpyAsync(host, s->state, bytes, cudaMemcpyDeviceToHost, s->stream));
   QS_CUDA(cudaStreamSynchronize(s->stream));
   if (r0r1) {
@@ -416,6 +452,7 @@ extern "C" qs_status sim_copy_in(qs_sim* s, const void* host, size_t bytes, cons
     CHECK_ARG(r0r1[0] >= 0 && r0r1[1] >= r0r1[0] && r0r1[1] < 1.0, "sim_copy_in: need 0 <= r0 <= r1 < 1");
     QS_TRY(a2_set_range(s, r0r1[0], r0r1[1]));
   }
+  s->zero_pending = false;   // every amplitude is written
   QS_CUDA(cudaMemcpyAsync(s->state, host, bytes, cudaMemcpyHostToDevice, s->stream));
   QS_CUDA(cudaStreamSynchronize(s->stream));
   return QS_OK;

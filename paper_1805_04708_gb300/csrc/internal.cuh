@@ -23,7 +23,15 @@ struct qs_sim {
   int device;
   int num_sms;
   int fused_engine;   // qs_fused_engine for apply_fused on complex64 states
+  bool lazy_reset;    // reset leaves |0..0> pending (library-owned states, or
+                      // borrowed ones whose owner asked for it)
+  bool zero_pending;  // the state is |0..0> but not written yet: the first
+                      // tile pass makes its tiles instead of loading them,
+                      // every other call that touches the amplitudes writes
+                      // them first
 };
+// Write a pending |0..0> (no-op otherwise).
+qs_status materialize_state(qs_sim* s);
 
 // error reporting ------------------------------------------------------------
 void qs_set_error(const char* fmt, ...);

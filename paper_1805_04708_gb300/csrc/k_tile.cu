@@ -74,7 +74,8 @@ static void mat_mul2(const double* b, const double* a, double* u) {
 // none of their qubits (a control acts diagonally too), so each diagonal gate
 // is delayed until a non-diagonal gate targets its target or one of its
 // controls, or the pass ends; the delayed gates are emitted together.  Then neighbouring gates with the same
-// target and the same controls are multiplied into one 2x2 (FP64, host).
+// target and the same controls, both diagonal or both not, are multiplied
+// into one 2x2 (FP64, host).
 static int rewrite_pass(const qs_gate* gates, const int* gidx, int ng, qs_gate* out) {
   int n = 0;
   int pend[MAX_TOPS * 2];
@@ -97,10 +98,13 @@ static int rewrite_pass(const qs_gate* gates, const int* gidx, int ng, qs_gate* 
     out[n++] = g;
   }
   for (int k = 0; k < np; ++k) out[n++] = gates[pend[k]];
-  // compose neighbours with equal (target, controls)
+  // compose neighbours with equal (target, controls), both diagonal or both
+  // not: a diagonal times a real or Hadamard-shaped gate is a general complex
+  // matrix, dearer than the two (the diagonal folds or costs one multiply)
   int m = 0;
   for (int i = 0; i < n; ++i) {
-    if (m > 0 && out[m - 1].target == out[i].target && same_controls(out[m - 1], out[i])) {
+    if (m > 0 && out[m - 1].target == out[i].target && same_controls(out[m - 1], out[i]) &&
+        is_diag_gate(out[m - 1]) == is_diag_gate(out[i])) {
       double u[8];
       mat_mul2(out[i].u, out[m - 1].u, u);
       memcpy(out[m - 1].u, u, sizeof u);
@@ -611,8 +615,13 @@ static qs_status emit_pass(PassSink& k, const TileParams2& P) {
 static qs_status run_pass(PassSink& k, const qs_gate* gates, const int* gidx, int ng, uint64_t tile) {
   static thread_local TileParams2 P;
   const int b = tile_bits(k.enc);
-  if (build_pass(gates, gidx, ng, k.N, b, tile_register_bits(k.enc), tile, &P, k.enc == QS_C64))
-    return emit_pass(k, P);
+  if (build_pass(gates, gidx, ng, k.N, b, tile_register_bits(k.enc), tile, &P, k.enc == QS_C64)) {
+    // a pending |0..0> is made by the first pass instead of being loaded
+    P.from_zero = (k.s && k.s->zero_pending) ? 1 : 0;
+    QS_TRY(emit_pass(k, P));
+    if (P.from_zero) k.s->zero_pending = false;
+    return QS_OK;
+  }
   // too many ops for one launch: split the gate run in halves (same tile)
   const int h = ng / 2;
   QS_TRY(run_pass(k, gates, gidx, h, tile));

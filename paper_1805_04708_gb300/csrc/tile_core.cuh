@@ -64,6 +64,8 @@ struct TileParams2 {
   TMap init, fin;      // register / warp assignment at load and at store
   int nops;
   int last_xpose;      // index of the last transpose op, -1 if none
+  int from_zero;       // the state is |0..0> and not in memory: tiles start as
+                       // zeros (amplitude 1 at index 0), nothing is loaded
   TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
   TMap maps[16];
   // T_DIAG_TAB: the factor of register j, complex64 (re, im) float bits in
@@ -385,13 +387,21 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
   const uint32_t tl_in = thread_part(P.init, lane, warp);
   const uint64_t ntiles = 1ull << (P.N - P.b);
   Cx<R> v[NR];
-  if (blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
+  const bool load = !P.from_zero;
+  if (load && blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
     const uint64_t base = deposit_t(tau, P.out_mask);
-    cp_async_wait_all();
-    unstage_tile<R, RB>(stg, v, P.init, tl_in);
+    if (load) {
+      cp_async_wait_all();
+      unstage_tile<R, RB>(stg, v, P.init, tl_in);
+    } else {
+      // |0..0>: register 0 of thread 0 of the tile at base 0 is index 0
+#pragma unroll
+      for (int j = 0; j < NR; ++j) v[j] = cx<R>((R)0, (R)0);
+      if (base == 0 && woff_in == 0) v[0] = cx<R>((R)1, (R)0);
+    }
     const uint64_t nxt = tau + gridDim.x;
-    if (P.last_xpose < 0 && nxt < ntiles)
+    if (load && P.last_xpose < 0 && nxt < ntiles)
       stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
     TMap cur = P.init;
     uint32_t tl = thread_part(cur, lane, warp);
@@ -434,7 +444,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
           }
         }
         __syncthreads();
-        if (i == P.last_xpose && nxt < ntiles)
+        if (load && i == P.last_xpose && nxt < ntiles)
           stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
         continue;
       }

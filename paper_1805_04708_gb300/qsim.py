@@ -73,6 +73,7 @@ _SIGS = {
     "sim_destroy": (_I, [_P]),
     "sim_info": (_I, [_P, _IP, _IP, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
     "sim_reset": (_I, [_P]),
+    "sim_set_lazy_reset": (_I, [_P, _I]),
     "apply_gate": (_I, [_P, _I, _D]),
     "apply_controlled": (_I, [_P, _IP, _I, _I, _D]),
     "apply_fused": (_I, [_P, _IP, _I, _D]),
@@ -209,7 +210,8 @@ class Sim:
             stream = torch.cuda.current_stream()
         self.stream_handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         nbytes = AMP_BYTES[self.enc] << self.N
-        if buffer is None:
+        own = buffer is None
+        if own:
             buffer = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         self._buf = buffer
         ptr = buffer.data_ptr()
@@ -219,6 +221,8 @@ class Sim:
         _check(_lib.sim_create_in(self.N, self.enc, _P(ptr_al), avail, _P(self.stream_handle), ctypes.byref(h)))
         self._h = h
         self.nbytes = nbytes
+        if own:   # the buffer is private: resets may stay pending
+            _check(_lib.sim_set_lazy_reset(h, 1))
 
     # -- lifetime --
     def close(self):

@@ -77,6 +77,43 @@ def test_tile_pass_packing(q, enc, N):
 
 
 @pytest.mark.parametrize("enc", ["c128", "c64"])
+def test_reset_then_every_access(q, enc):
+    # a reset state is |0..0> whichever call reads or writes it first: the
+    # first tile pass makes its tiles, every other call writes the state first
+    N = 14
+    recs = wl.random_gate_circuit(N, 60, seed=4)
+    ref = circuit.run(sv.zero_state(N), N, recs)
+    e0 = sv.zero_state(N)
+    with q.Sim(N, enc) as s:
+        s.circuit_run(recs, mode=1)
+        s.reset()
+        s.circuit_run(recs, mode=1)               # first pass starts from |0..0>
+        assert maxerr(s.copy_out(), ref) <= TOL[enc]
+        s.reset()
+        assert maxerr(s.copy_out(), e0) == 0.0
+        s.circuit_run(recs, mode=1)
+        s.reset()
+        assert abs(s.norm() - 1.0) == 0.0
+        s.reset()
+        p = s.measure_probs([0, 1, 2])
+        assert p[0] == 1.0 and np.all(p[1:] == 0.0)
+        s.reset()
+        qx, qy, qz = s.expect_xyz()
+        assert np.allclose(qz, 0.0, atol=0) and np.allclose(qx, 0.5, atol=1e-15)
+        s.reset()
+        s.apply_gate(3, np.array([[1, 1], [1, -1]]) / np.sqrt(2))
+        want = np.zeros(1 << N, complex)
+        want[0] = want[8] = 2 ** -0.5
+        assert maxerr(s.copy_out(), want) <= TOL[enc]
+        s.reset()
+        # the device pointer: the caller may read the memory directly
+        ptr = s.device_ptr()
+        s.sync()
+        p = q.measure_probs_static(ptr, N, enc, [0, 5, 13])
+        assert p[0] == 1.0 and np.all(p[1:] == 0.0)
+
+
+@pytest.mark.parametrize("enc", ["c128", "c64"])
 def test_every_gate_every_position(q, enc):
     N = 6
     names = ["H", "X", "Y", "Z", "S", "S+", "T", "T+", "+X", "-X", "+Y", "-Y"]
