@@ -43,10 +43,11 @@ UNIT = "updates/s"
 # (2 * 2^N * 8 B for complex64)
 # DRAM bytes per tile-pass launch at N = 30, from one ncu capture of the
 # N = 26 random-gate circuit in circuit_run mode 2 (after its kernel choice;
-# interpreter and compiled passes) scaled
-# by the 16x units (profiles/tile_pass_c64_n26_traffic.md); None when a pass
-# kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = 1.6275e10
+# interpreter and compiled passes), as the mean over a step's 12 passes of
+# which the first only writes, scaled by the 16x units
+# (profiles/tile_pass_c64_n26_traffic.md); None when a pass kernel changes
+# after the capture
+TILE_TRAFFIC_PER_PASS = 1.5566e10
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
@@ -457,10 +458,13 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: the complex64 tile pass
     peak, peak_kind = load_peaks()
-    alg_bytes = 2.0 * (8 << N)
+    # algorithmic bytes: every pass reads and writes the state once, except
+    # the first of a step, which starts from the pending |0..0> of the reset
+    # and only writes; per launch = the step's bytes over its passes
+    passes_per_step = len(pass_ms) // args.steps
+    alg_bytes = (2.0 * passes_per_step - 1.0) * (8 << N) / passes_per_step
     mean_pass = sum(pass_ms) / len(pass_ms)
     achieved = alg_bytes / (mean_pass / 1e3) / 1e9
-    passes_per_step = len(pass_ms) // args.steps
     roofline = {"kernel": "complex64 tile pass (%s)" % TILE_MODES[mode], "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
