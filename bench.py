@@ -523,6 +523,8 @@ def run_profile_case(args):
                kernel candidate, four times), then <Qx,Qy,Qz> (complex64)
       fused  : a dense k-qubit gate on qubits 0..k-1, applied three times
                (complex64; the tcgen05 kernel for k >= 3)
+      adapt2 : one Haar U(2) on every qubit of the adaptive 2-byte state
+               (the range and encode passes of each arithmetic gate)
       expect : BEGIN MEASUREMENT (<Qx,Qy,Qz> of every qubit) twice on the
                state after the random-gate circuit (complex64)
       ops    : four single-pass circuits of one op class each (complex64):
@@ -533,6 +535,13 @@ def run_profile_case(args):
     from paper_1805_04708_gb300 import qsim
     from paper_1805_04708_gb300 import workloads as wl
     N = args.qubits
+    if args.profile_case == "adapt2":
+        recs = [r for r in wl.layered_circuit(N, 1, seed=1) if len(r[1]) == 1]
+        with qsim.Sim(N, "adapt2") as s:
+            s.circuit_run(recs, mode=1)
+            print("profile case adapt2 N=%d gates %d norm %.6f" % (N, len(recs), s.norm()))
+        torch.cuda.synchronize()
+        return 0
     with qsim.Sim(N, "c64") as s:
         if args.profile_case == "tile" and args.mode == 2:
             # compile, then one run per kernel candidate of every pass structure
@@ -580,7 +589,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", choices=["tile", "fused", "ops", "expect"], default=None,
+    ap.add_argument("--profile-case", choices=["tile", "fused", "ops", "expect", "adapt2"], default=None,
                     help="run a small workload for a profiler and exit")
     ap.add_argument("--qubits", type=int, default=26)
     ap.add_argument("--k", type=int, default=5)

@@ -64,13 +64,21 @@ __device__ EncP enc_params(const A2Dev* d) {
   return e;
 }
 
-__device__ __forceinline__ void track(Cx<float> z, float& mn, float& mx) {
-  const float m = a2_mag(z);
-  if (m > 0.f && m < 1.f) { mn = fminf(mn, m); mx = fmaxf(mx, m); }
+// Range tracking on squared magnitudes: sqrtf is monotonic, so the min / max
+// of sqrtf(m2) is sqrtf of the min / max of m2 (taken once per thread in
+// block_minmax), and for a float m2, sqrtf(m2) < 1 exactly when m2 < 1 (the
+// float below 1 has its root below the midpoint of 1 - 2^-24 and 1) and
+// sqrtf(m2) > 0 exactly when m2 > 0.
+__device__ __forceinline__ void track(Cx<float> z, float& mn2, float& mx2) {
+  const float m2 = fmaf(z.x, z.x, z.y * z.y);
+  if (m2 > 0.f && m2 < 1.f) { mn2 = fminf(mn2, m2); mx2 = fmaxf(mx2, m2); }
 }
 
-__device__ void block_minmax(float mn, float mx, A2Dev* d) {
+// mn2 / mx2: the thread's min / max of squared magnitudes (INF / 0 if none)
+__device__ void block_minmax(float mn2, float mx2, A2Dev* d) {
   __shared__ float smn[32], smx[32];
+  float mn = (mn2 < __uint_as_float(INF_BITS)) ? sqrtf(mn2) : mn2;
+  float mx = sqrtf(mx2);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
