@@ -97,6 +97,14 @@ struct OpRealF {
     a1 = cx<float>(B1.x, B1.y);
   }
 };
+// Unscaled Hadamard butterfly (a0 + a1, a0 - a1).
+template <typename R> struct OpBfly {
+  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
+    const Cx<R> b0 = cx<R>(a0.x + a1.x, a0.y + a1.y), b1 = cx<R>(a0.x - a1.x, a0.y - a1.y);
+    a0 = b0;
+    a1 = b1;
+  }
+};
 // Unscaled Hadamard butterfly on complex64 pairs: one packed instruction per
 // output (the pass applies the dropped scale factors elsewhere, once).
 struct OpBflyF {

@@ -335,18 +335,19 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
     }
     nops = m;
   }
-  // complex64: uncontrolled ops of the form s [[1, 1], [1, -1]] (Hadamards)
-  // become unscaled butterflies (coefficients [[1, 1], [1, -1]]); the product
-  // of their scales, a scalar that commutes with every op, goes into the
-  // first factor table of the pass, else into an uncontrolled real or dense
-  // op, else stays with one of the Hadamards
-  if (real_kinds) {
+  // uncontrolled ops of the form s [[1, 1], [1, -1]] (Hadamards) become
+  // unscaled butterflies (coefficients [[1, 1], [1, -1]]); the product of
+  // their scales, a scalar that commutes with every op, goes into the first
+  // factor table of the pass, else into an uncontrolled real or dense op,
+  // else stays with one of the Hadamards
+  {
     auto unc = [&](const TOp& o) {
       return (o.type == T_REG || o.type == T_LANE) && o.smask == 0 && o.tmask == 0 && o.gmask == 0;
     };
     auto had_scale = [&](const TOp& o) -> double {
       const double* u = o.ud;
-      if (o.kind != GK_REAL || u[1] != 0.0 || u[3] != 0.0 || u[5] != 0.0 || u[7] != 0.0) return 0.0;
+      if (o.kind != (real_kinds ? GK_REAL : GK_HAD) || u[1] != 0.0 || u[3] != 0.0 || u[5] != 0.0 || u[7] != 0.0)
+        return 0.0;
       if (!(u[0] > 0.0) || u[2] != u[0] || u[4] != u[0] || u[6] != -u[0]) return 0.0;
       return u[0];
     };
@@ -379,7 +380,7 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
       } else {
         if (carrier < 0) {   // one of the Hadamards keeps the whole scale
           carrier = first_h;
-          P->ops[carrier].kind = GK_REAL;
+          P->ops[carrier].kind = real_kinds ? GK_REAL : GK_HAD;
         }
         TOp& c = P->ops[carrier];
         double u[8];

@@ -260,6 +260,9 @@ __device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, in
         v[j] = hi ? cx<R>((a0.x - a1.x) * s, (a0.y - a1.y) * s) : cx<R>((a0.x + a1.x) * s, (a0.y + a1.y) * s);
         break;
       }
+      case GK_BFLY:
+        v[j] = hi ? cx<R>(a0.x - a1.x, a0.y - a1.y) : cx<R>(a0.x + a1.x, a0.y + a1.y);
+        break;
       case GK_ANTI:
         v[j] = hi ? cmul_code(a0, u10, st.c1) : cmul_code(a1, u01, st.c0);
         break;
@@ -490,6 +493,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
             // complex128: the FP64 pipe is the bound, so keep the cheaper forms
             switch (st.kind) {
               case GK_HAD: { OpHad<R> f; f.s = uscal<R>(o); reg_op<R, RB>(v, st.a, st.smask, f); break; }
+              case GK_BFLY: { OpBfly<R> f; reg_op<R, RB>(v, st.a, st.smask, f); break; }
               case GK_ANTI: { OpAnti<R> f; f.f01 = ucx<R>(o, 1); f.f10 = ucx<R>(o, 2); f.c0 = st.c0; f.c1 = st.c1; reg_op<R, RB>(v, st.a, st.smask, f); break; }
               default: {
                 OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
