@@ -6,8 +6,7 @@
 
 struct Luts {
   float r[256];     // magnitude for b0 + 128
-  float c[256];     // cos(pi b1 / 128) for b1 + 128
-  float s[256];
+  float2 cs[256];   // (cos, sin)(pi b1 / 128) for b1 + 128: one 8-byte lookup
 };
 
 // Every thread of the block must call this (it synchronises).
@@ -26,8 +25,7 @@ static __device__ void build_luts(Luts& L, double r0, double r1) {
     double sn, cs;
     sincospi((double)k / 128.0, &sn, &cs);
     for (int q = 0; q < turns; ++q) { const double t = cs; cs = -sn; sn = t; }
-    L.c[i] = (float)cs;
-    L.s[i] = (float)sn;
+    L.cs[i] = make_float2((float)cs, (float)sn);
   }
   __syncthreads();
 }
@@ -36,6 +34,7 @@ static __device__ __forceinline__ Cx<float> a2_dec(const Luts& L, unsigned int w
   const int b0 = (int)(w & 0xFFu) ^ 0x80;         // b0 + 128
   const int b1 = (int)((w >> 8) & 0xFFu) ^ 0x80;  // b1 + 128
   const float r = L.r[b0];
-  return cx<float>(r * L.c[b1], r * L.s[b1]);
+  const float2 t = L.cs[b1];
+  return cx<float>(r * t.x, r * t.y);
 }
 
