@@ -217,6 +217,15 @@ qs_status circuit_run(qs_sim* sim, const qs_gate* gates, int n, int mode, int* n
  * circuit_run. */
 qs_status circuit_compile(int N, const qs_gate* gates, int n, int mode, int* n_passes);
 
+/* The order in which circuit_run's tile passes take the gates (host only, no
+ * device call): for a QS_C64 or QS_C128 circuit on N >= 13 (QS_C64) / 12
+ * (QS_C128) qubits, order (host, n ints) receives the indices of the
+ * non-identity gates in run order and pass_start (host, n ints) the position
+ * in order where each pass begins; *n_passes the number of passes.  Inside a
+ * pass the op rewriting (delayed diagonals, composed neighbours, factor
+ * tables) is not shown.  The paper has no counterpart. */
+qs_status circuit_plan(int N, int enc, const qs_gate* gates, int n, int* order, int* pass_start, int* n_passes);
+
 /* Whether NVRTC could be loaded (available: 1 or 0) and how many pass
  * kernels this process has compiled so far (compiles).  Outputs may be NULL. */
 qs_status tile_compiler_info(int* available, long* compiles);

@@ -356,6 +356,19 @@ extern "C" qs_status circuit_compile(int N, const qs_gate* gates, int n, int mod
   return compile_tile_passes(N, gates, n, n_passes, mode == 3);
 }
 
+extern "C" qs_status circuit_plan(int N, int enc, const qs_gate* gates, int n, int* order, int* pass_start,
+                                  int* n_passes) {
+  CHECK_ARG(enc == QS_C128 || enc == QS_C64, "circuit_plan: encoding %d has no tile passes", enc);
+  CHECK_ARG(N >= tile_bits((qs_encoding)enc) && N < 64, "circuit_plan: N = %d below the tile size", N);
+  CHECK_ARG(n >= 0 && (n == 0 || gates != nullptr), "circuit_plan: bad gate list");
+  CHECK_ARG(order != nullptr && pass_start != nullptr && n_passes != nullptr, "circuit_plan: null output");
+  qs_sim probe;
+  probe.N = N;
+  probe.enc = (qs_encoding)enc;
+  for (int i = 0; i < n; ++i) QS_TRY(check_gate(&probe, gates[i]));
+  return plan_tile_pass_order(N, (qs_encoding)enc, gates, n, order, pass_start, n_passes);
+}
+
 extern "C" qs_status tile_compiler_info(int* available, long* compiles) {
   if (available) *available = tile_jit_available() ? 1 : 0;
   if (compiles) *compiles = tile_jit_compiles();

@@ -123,6 +123,11 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
 // circuit_run mode 3 launches (all_passes) or every compiled candidate of
 // mode 2.
 qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes);
+// The planner's pass order (host only): order gets the non-identity gate
+// indices in the order the passes take them, pass_start the first position
+// of each pass (both sized n by the caller).
+qs_status plan_tile_pass_order(int N, qs_encoding enc, const qs_gate* gates, int n, int* order, int* pass_start,
+                               int* n_passes);
 
 // ADAPT2 --------------------------------------------------------------------------
 // Device-resident range of the adaptive encoding (Sec. 4.1): the current

@@ -436,6 +436,8 @@ struct PassSink {
   PassTimer* timer;
   int emitted;
   std::vector<JitJob>* collect;   // compile only: the kernels to compile
+  std::vector<int>* plan;         // plan only: gate indices in run order
+  std::vector<int>* plan_start;   // plan only: first index of each pass
 };
 
 static qs_status emit_pass(PassSink& k, const TileParams2& P);
@@ -519,7 +521,7 @@ static qs_status plan_tile_passes(PassSink& k, const qs_gate* gates, int n) {
 }
 
 qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer, int jit) {
-  PassSink k = {s, s->N, s->enc, 0, timer, 0, nullptr};
+  PassSink k = {s, s->N, s->enc, 0, timer, 0, nullptr, nullptr, nullptr};
   if (s->enc == QS_C64 && jit != 0) {
     if (!tile_jit_available()) {
       qs_set_error("circuit_run: compiled tile passes need NVRTC, which could not be loaded");
@@ -534,10 +536,21 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
 
 qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes) {
   std::vector<JitJob> passes;
-  PassSink k = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes};
+  PassSink k = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes, nullptr, nullptr};
   QS_TRY(plan_tile_passes(k, gates, n));
   if (n_passes) *n_passes = k.emitted;
   return tile_jit_compile_all(passes);
+}
+
+qs_status plan_tile_pass_order(int N, qs_encoding enc, const qs_gate* gates, int n, int* order, int* pass_start,
+                               int* n_passes) {
+  std::vector<int> plan, start;
+  PassSink k = {nullptr, N, enc, 0, nullptr, 0, nullptr, &plan, &start};
+  QS_TRY(plan_tile_passes(k, gates, n));
+  for (size_t i = 0; i < plan.size(); ++i) order[i] = plan[i];
+  for (size_t i = 0; i < start.size(); ++i) pass_start[i] = start[i];
+  *n_passes = (int)start.size();
+  return QS_OK;
 }
 
 static qs_status launch_pass(PassSink& k, const TileParams2& P) {
@@ -616,6 +629,12 @@ static qs_status emit_pass(PassSink& k, const TileParams2& P) {
 static qs_status run_pass(PassSink& k, const qs_gate* gates, const int* gidx, int ng, uint64_t tile) {
   static thread_local TileParams2 P;
   const int b = tile_bits(k.enc);
+  if (k.plan) {   // plan only: the pass's gates in the order it takes them
+    k.plan_start->push_back((int)k.plan->size());
+    for (int j = 0; j < ng; ++j) k.plan->push_back(gidx[j]);
+    ++k.emitted;
+    return QS_OK;
+  }
   if (build_pass(gates, gidx, ng, k.N, b, tile_register_bits(k.enc), tile, &P, k.enc == QS_C64)) {
     // a pending |0..0> is made by the first pass instead of being loaded
     P.from_zero = (k.s && k.s->zero_pending) ? 1 : 0;

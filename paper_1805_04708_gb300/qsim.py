@@ -84,6 +84,7 @@ _SIGS = {
     "circuit_run": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP]),
     "circuit_compile": (_I, [_I, ctypes.POINTER(qs_gate), _I, _I, _IP]),
     "tile_compiler_info": (_I, [_IP, ctypes.POINTER(ctypes.c_long)]),
+    "circuit_plan": (_I, [_I, _I, ctypes.POINTER(qs_gate), _I, _IP, _IP, _IP]),
     "circuit_run_timed": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP, ctypes.POINTER(ctypes.c_float), _I]),
     "gate_std": (_I, [ctypes.c_char_p, _IP, _I, _D, _I, ctypes.POINTER(qs_gate)]),
     "sim_norm": (_I, [_P, _D]),
@@ -180,6 +181,25 @@ def circuit_compile(N, gates, mode=2):
     npass = ctypes.c_int(0)
     _check(_lib.circuit_compile(int(N), arr, n, int(mode), ctypes.byref(npass)))
     return npass.value
+
+
+def circuit_plan(N, gates, enc="c64"):
+    """The tile passes' gate order (host only): a list of passes, each the
+    list of gate indices (into `gates`) in the order the pass takes them
+    (identity gates are dropped)."""
+    if isinstance(gates, tuple):
+        arr, n = gates
+    else:
+        arr, n = gate_array(gates)
+    order = np.full(max(1, n), -1, dtype=np.int32)
+    start = np.zeros(max(1, n), dtype=np.int32)
+    npass = ctypes.c_int(0)
+    e = ENCODINGS[enc] if isinstance(enc, str) else int(enc)
+    _check(_lib.circuit_plan(int(N), e, arr, n, order.ctypes.data_as(_IP), start.ctypes.data_as(_IP),
+                             ctypes.byref(npass)))
+    used = int(np.count_nonzero(order[:n] >= 0))
+    bounds = [int(x) for x in start[:npass.value]] + [used]
+    return [[int(x) for x in order[bounds[i]:bounds[i + 1]]] for i in range(npass.value)]
 
 
 def tile_compiler_info():
