@@ -198,7 +198,8 @@ qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
  *           handle's stream; later launches use the fastest.  Compiled
  *           kernels are cached; a new structure pays its compile time unless
  *           circuit_compile ran first; a variant that fails to compile is
- *           never picked;
+ *           never picked.  Compiled kernels (a few hundred KB each) stay
+ *           loaded until the process ends;
  *   mode 3: the compiled kernel without barriers for every QS_C64 pass.
  * Modes 2 and 3 give QS_EUNSUPPORTED on a QS_C64 state when NVRTC cannot be
  * loaded; QS_C128 states use the interpreter in every tile mode.  Results
