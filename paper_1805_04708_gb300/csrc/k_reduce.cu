@@ -10,6 +10,7 @@
 #include "internal.cuh"
 #include "cplx.cuh"
 #include "a2codec.cuh"
+#include "tma.cuh"
 #include <string.h>
 
 namespace {
@@ -179,7 +180,8 @@ __global__ void __launch_bounds__(TPB) k_expect_small(const A* __restrict__ s, i
   }
 }
 
-// ---- expect_xyz: register-tile passes -----------------------------------------------------
+// ---- expect_xyz for complex128: register-tile passes ---------------------------------------
+// (complex64 and the adaptive words use the shared-memory views further down.)
 // A pass reads the state once in tiles of 2^(RB+8) amplitudes: inside a CTA of
 // 256 threads, local bit 0 and RB-1 chosen qubits are register slots (each
 // thread holds 2^RB amplitudes), index bits 1..5 are the 32 lanes, and 3 more
@@ -190,10 +192,9 @@ __global__ void __launch_bounds__(TPB) k_expect_small(const A* __restrict__ s, i
 // bit and per tile and warp (from which P_n(1) of every qubit follows); later
 // passes compute w_n for RB-1 new slot qubits each.
 //
-// Per-thread sums are formed per tile in the arithmetic type (FP32 for
-// complex64, FP64 for complex128) and folded into per-thread accumulators in
-// shared memory (float-float / FP64), then reduced over the CTA and the grid
-// in a fixed order.
+// Per-thread sums are formed per tile in FP64 and folded into per-thread
+// accumulators in shared memory, then reduced over the CTA and the grid in a
+// fixed order.
 constexpr int ETPB = 256;
 
 struct RedParams {
@@ -206,21 +207,6 @@ struct RedParams {
 };
 
 template <typename R> struct SAcc;
-template <> struct SAcc<float> {
-  // float-float accumulators, [acc][thread] in shared memory
-  float* hi; float* lo;
-  __device__ void init(unsigned char* base, int nacc) {
-    hi = (float*)base; lo = hi + nacc * ETPB;
-    for (int i = 0; i < nacc; ++i) { hi[i * ETPB + threadIdx.x] = 0.f; lo[i * ETPB + threadIdx.x] = 0.f; }
-  }
-  __device__ __forceinline__ void add(int i, float x) {
-    FF f = {hi[i * ETPB + threadIdx.x], lo[i * ETPB + threadIdx.x]};
-    ff_add(f, x);
-    hi[i * ETPB + threadIdx.x] = f.hi; lo[i * ETPB + threadIdx.x] = f.lo;
-  }
-  __device__ double get(int i) const { return (double)hi[i * ETPB + threadIdx.x] + (double)lo[i * ETPB + threadIdx.x]; }
-  __host__ __device__ static size_t bytes(int nacc) { return (size_t)nacc * ETPB * 8; }
-};
 template <> struct SAcc<double> {
   double* a;
   __device__ void init(unsigned char* base, int nacc) {
@@ -257,14 +243,11 @@ __device__ __forceinline__ void slot_w_rt(const Cx<R>* v, int s, R& re, R& im) {
   }
 }
 
-// ENC: 0 complex64, 1 complex128, 2 adaptive 2-byte words (decoded to FP32)
-template <typename R, int RB, int ENC>
+template <typename R, int RB>
 __global__ void __launch_bounds__(ETPB, 2) k_expect2(const void* __restrict__ s, const __grid_constant__ RedParams P,
-                                                      double* __restrict__ tile_tot, double* __restrict__ part,
-                                                      const A2Dev* __restrict__ a2) {
+                                                      double* __restrict__ tile_tot, double* __restrict__ part) {
+  static_assert(sizeof(R) == 8, "complex128 only");
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ Luts L;
-  if (ENC == 2) build_luts(L, a2->r0, a2->r1);
   constexpr int NR = 1 << RB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // accumulators: pass 0: [w re/im: slot 0, lanes 0..4, slots 1..ns] [P1: slots 0..RB-1, lanes 0..4]
@@ -288,30 +271,12 @@ __global__ void __launch_bounds__(ETPB, 2) k_expect2(const void* __restrict__ s,
   Cx<R> v[NR];
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
     const uint64_t base = deposit(tau, P.out_mask) | woff;
-    if constexpr (ENC == 2) {
-      const unsigned int* s2 = (const unsigned int*)s;
+    const double2* s2 = (const double2*)s;
 #pragma unroll
-      for (int jj = 0; jj < NR / 2; ++jj) {
-        const unsigned int w = s2[(base + roff[jj]) >> 1];
-        v[2 * jj] = a2_dec(L, w & 0xFFFFu);
-        v[2 * jj + 1] = a2_dec(L, w >> 16);
-      }
-    } else if constexpr (sizeof(R) == 4) {
-      const float4* s4 = (const float4*)s;
-#pragma unroll
-      for (int jj = 0; jj < NR / 2; ++jj) {
-        float4 x = s4[(base + roff[jj]) >> 1];
-        v[2 * jj] = cx<float>(x.x, x.y);
-        v[2 * jj + 1] = cx<float>(x.z, x.w);
-      }
-    } else {
-      const double2* s2 = (const double2*)s;
-#pragma unroll
-      for (int jj = 0; jj < NR / 2; ++jj) {
-        double2 x = s2[base + roff[jj]], y = s2[base + roff[jj] + 1];
-        v[2 * jj] = cx<double>(x.x, x.y);
-        v[2 * jj + 1] = cx<double>(y.x, y.y);
-      }
+    for (int jj = 0; jj < NR / 2; ++jj) {
+      double2 x = s2[base + roff[jj]], y = s2[base + roff[jj] + 1];
+      v[2 * jj] = cx<double>(x.x, x.y);
+      v[2 * jj + 1] = cx<double>(y.x, y.y);
     }
     int ai = 0;
     if (P.first) {
@@ -396,6 +361,276 @@ __global__ void k_tile_bits(const double* __restrict__ tile_tot, uint64_t ntiles
     if (threadIdx.x == 0) part[(size_t)blockIdx.x * (nq_out + 1) + i] = r;
     __syncthreads();
   }
+}
+
+// ---- expect_xyz for complex64 and adaptive words: shared-memory views ------------------
+// A tile is 2^13 amplitudes: local bits 0..3 are index bits 0..3 (128-byte
+// runs of complex64), local bits 4..3+f the qubits 4..3+f and local bits
+// 4+f..12 a run of 9-f consecutive qubits b..b+8-f.  Pass 0 takes qubits
+// 0..12 (f = 0, b = 4); the later passes split qubits 13..N-1 into runs of
+// near-equal length (at most 9), each padded with the low qubits 4.. (already
+// served).  Each of 256 threads holds 32 amplitudes of the tile in
+// registers, in one of three views (register bits; the thread index covers
+// the other 8 local bits):
+//   view A: local {0, 6, 7, 8, 9}    lanes = local 1..5, warps = local 10..12
+//   view B: local {4, 5, 10, 11, 12}
+//   view C: local {1, 2, 3, 7, 8}    (the last pass only)
+// A qubit that is a register bit of a view gets w_n from pairs held by one
+// thread, so pass 0 serves qubits 0 and 4..12, the last pass qubits 1..3,
+// and every later pass up to 9 new qubits (3 passes at N = 30: 0..12,
+// 13..21, 4 + 22..29).  Splitting the runs evenly keeps a tile within 2^8 of
+// the 2 MB pages of the state where it can: tiles spread over 2^9 pages
+// measured 1.1-1.5x slower.  The tile sits in shared memory in the 128-byte swizzle
+// of the tensor loads (complex64 units: local bits 4..6 flip bits 1..3),
+// under which all three views read without bank conflicts.
+//
+// Per tile each thread forms FP32 leaf sums (at most 16 pairs or 16 |a|^2)
+// and folds them into float-float accumulators in registers; the CTA sums
+// those in FP64 in a fixed order at the end, the grid by k_sum_columns.
+namespace xv {
+constexpr int TB = 13;      // tile bits
+constexpr int NV = 16;      // values per view: w re/im of 5 slots, then P1 of 5 slots
+constexpr int NVIEW = 3;
+constexpr int NCOL = NV * NVIEW;
+constexpr uint8_t REG_A[5] = {0, 6, 7, 8, 9};
+constexpr uint8_t REG_B[5] = {4, 5, 10, 11, 12};
+constexpr uint8_t REG_C[5] = {1, 2, 3, 7, 8};
+__host__ __device__ constexpr uint32_t phys(uint32_t l) { return l ^ (((l >> 4) & 7u) << 1); }
+__host__ __device__ constexpr uint32_t reg_a(int j) { return (uint32_t)(j & 1) | ((uint32_t)(j >> 1) << 6); }
+__host__ __device__ constexpr uint32_t reg_b(int j) { return ((uint32_t)(j & 3) << 4) | ((uint32_t)(j >> 2) << 10); }
+__host__ __device__ constexpr uint32_t reg_c(int j) { return ((uint32_t)(j & 7) << 1) | ((uint32_t)(j >> 3) << 7); }
+__device__ __forceinline__ uint32_t thr_a(int t) { return ((uint32_t)(t & 31) << 1) | ((uint32_t)(t >> 5) << 10); }
+__device__ __forceinline__ uint32_t thr_b(int t) { return (uint32_t)(t & 15) | ((uint32_t)(t >> 4) << 6); }
+__device__ __forceinline__ uint32_t thr_c(int t) {
+  return (uint32_t)(t & 1) | ((uint32_t)((t >> 1) & 7) << 4) | ((uint32_t)(t >> 4) << 9);
+}
+}  // namespace xv
+
+struct XParams {
+  int N;
+  int f, b;               // local bits 4..3+f: qubits 4..3+f; 4+f..12: qubits b..b+8-f
+  int lo_bits;            // tile-index bits below the run (qubits 4+f..b-1)
+  uint64_t out_mask;      // global bits outside the tile
+  uint64_t roff_a[16];    // register loads: global offset of view-A register pair (2jj, 2jj+1)
+  uint8_t gpos[16];       // global qubit of local bit k
+};
+
+// Per-thread float-float accumulators of one pass: view A and B hold w re/im
+// of their 5 register slots (and in the first pass P1 of each slot), view C
+// (VC: the last pass, whose ALU load is lighter) w and P1 of its slots 0..2,
+// qubits 1..3, which every tile holds.
+template <bool FIRST, bool VC>
+struct XAcc {
+  static constexpr int NA = FIRST ? 15 : 10, NC = VC ? 9 : 0, N = 2 * NA + NC;
+  FF f[N];
+  // output column of accumulator i (16 columns per view: w re/im of slot s at
+  // 2s, 2s+1, P1 of slot s at 10+s)
+  __host__ __device__ static constexpr int col(int i) {
+    return i < NA ? i : i < 2 * NA ? xv::NV + (i - NA) : 2 * xv::NV + (i - 2 * NA < 6 ? i - 2 * NA : 4 + (i - 2 * NA));
+  }
+};
+
+// Fold one view's per-thread leaf sums (FP32, at most 16 pairs each) into
+// acc[0 .. 2NS-1] (w re/im of slots 0..NS-1) and, with P1, acc[2NS ..
+// 3NS-1] (P1 of the slots); T = sum of all |a|^2 of the thread.
+template <int NS, bool P1>
+__device__ __forceinline__ void view_fold(const Cx<float>* v, FF* acc, float& T) {
+  float re, im;
+  slot_w<float, 5, 0>(v, re, im); ff_add(acc[0], re); ff_add(acc[1], im);
+  slot_w<float, 5, 1>(v, re, im); ff_add(acc[2], re); ff_add(acc[3], im);
+  slot_w<float, 5, 2>(v, re, im); ff_add(acc[4], re); ff_add(acc[5], im);
+  if constexpr (NS > 3) { slot_w<float, 5, 3>(v, re, im); ff_add(acc[6], re); ff_add(acc[7], im); }
+  if constexpr (NS > 4) { slot_w<float, 5, 4>(v, re, im); ff_add(acc[8], re); ff_add(acc[9], im); }
+  T = 0.f;
+  if constexpr (P1) {
+    // halving tree: at level s the sums over register bits < s are paired;
+    // P1 of slot s is the sum of the odd members of level s
+    float p[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) p[j] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+#pragma unroll
+    for (int sl = 0, n = 32; sl < 5; ++sl, n >>= 1) {
+      if (sl < NS) {
+        float q = p[1];
+#pragma unroll
+        for (int i = 3; i < n; i += 2) q += p[i];
+        ff_add(acc[2 * NS + sl], q);
+      }
+#pragma unroll
+      for (int i = 0; i < n / 2; ++i) p[i] = p[2 * i] + p[2 * i + 1];
+    }
+    T = p[0];
+  }
+}
+
+// View A is in v; folds it, then views C (VC) and B read from the shared
+// tile xt.  FIRST also writes the per-(tile, warp) total of |a|^2.
+template <bool FIRST, bool VC>
+__device__ __forceinline__ void tile_views(const float2* xt, Cx<float> (&v)[32], XAcc<FIRST, VC>& acc, uint64_t tau,
+                                           double* __restrict__ tile_tot) {
+  const int t = threadIdx.x;
+  constexpr int NA = XAcc<FIRST, VC>::NA;
+  float T;
+  view_fold<5, FIRST>(v, acc.f, T);
+  if (FIRST) {
+    const double tt = warp_sum((double)T);
+    if ((t & 31) == 0) tile_tot[tau * 8 + (t >> 5)] = tt;
+  }
+  if constexpr (VC) {
+    const uint32_t pc = xv::phys(xv::thr_c(t));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float2 q = xt[pc ^ xv::phys(xv::reg_c(j))];
+      v[j] = cx<float>(q.x, q.y);
+    }
+    view_fold<3, true>(v, acc.f + 2 * NA, T);
+  }
+  const uint32_t pb = xv::phys(xv::thr_b(t));
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float2 q = xt[pb ^ xv::phys(xv::reg_b(j))];
+    v[j] = cx<float>(q.x, q.y);
+  }
+  view_fold<5, FIRST>(v, acc.f + NA, T);
+}
+
+// CTA sum of the accumulators in FP64 in a fixed order (warp tree, then the 8
+// warps in order) into part[block][column]; red: XAcc::N * 8 doubles of
+// shared memory.  Columns no accumulator maps to are written as 0.
+template <bool FIRST, bool VC>
+__device__ __forceinline__ void views_to_part(const XAcc<FIRST, VC>& acc, double* red, double* __restrict__ part) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int M = XAcc<FIRST, VC>::N;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const double d = warp_sum((double)acc.f[i].hi + (double)acc.f[i].lo);
+    if (lane == 0) red[i * 8 + warp] = d;
+  }
+  __syncthreads();
+  if (t < xv::NCOL) part[(size_t)blockIdx.x * xv::NCOL + t] = 0.0;
+  __syncthreads();
+  if (t < M) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += red[t * 8 + w];
+    part[(size_t)blockIdx.x * xv::NCOL + XAcc<FIRST, VC>::col(t)] = sum;
+  }
+}
+
+// complex64: one persistent CTA per SM; thread 0 streams the CTA's tiles
+// through a ring of XSTAGES shared-memory buffers with 5-D tensor loads
+// (dims: qubits 0..3, the two tile segments, then the qubits below and above
+// the run: the tile index, low bits first), the whole CTA
+// consumes them in order.  A wait that runs out makes every thread leave the
+// loop; thread 0 then waits (bounded) for the loads still in flight and sets
+// *err.
+constexpr int XSTAGES = 3;
+constexpr uint32_t XTILE_BYTES = 8u << xv::TB;
+constexpr size_t XTMA_SMEM = (size_t)XSTAGES * XTILE_BYTES + 1024 + 64;
+
+template <bool FIRST, bool VC>
+__global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ CUtensorMap map,
+                                                         const __grid_constant__ XParams P,
+                                                         double* __restrict__ tile_tot, double* __restrict__ part,
+                                                         int* __restrict__ err) {
+  using namespace qs_tma;
+  extern __shared__ unsigned char xraw[];
+  const uint32_t raw_s = smem_u32(xraw);
+  unsigned char* buf = xraw + (((raw_s + 1023u) & ~1023u) - raw_s);   // the swizzle repeats every 1024 bytes
+  uint64_t* full = (uint64_t*)(buf + XSTAGES * XTILE_BYTES);
+  volatile int* abort_flag = (volatile int*)(full + XSTAGES);
+  const int t = threadIdx.x;
+  if (t == 0) {
+    for (int st = 0; st < XSTAGES; ++st) mbar_init(smem_u32(&full[st]), 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const uint64_t ntiles = 1ull << (P.N - xv::TB);
+  const uint64_t nmine = (uint64_t)blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int lo_bits = P.lo_bits;
+  uint64_t issued = 0;           // thread 0 only
+  auto issue = [&]() {
+    const uint64_t tau = blockIdx.x + issued * gridDim.x;
+    const int st = (int)(issued % XSTAGES);
+    const uint32_t bar = smem_u32(&full[st]);
+    mbar_expect_tx(bar, XTILE_BYTES);
+    tma_load_5d(smem_u32(buf + st * XTILE_BYTES), &map, 0, 0, 0, (int)(tau & ((1ull << lo_bits) - 1)),
+                (int)(tau >> lo_bits), bar);
+    ++issued;
+  };
+  if (t == 0)
+    while (issued < nmine && issued < (uint64_t)XSTAGES) issue();
+  const uint32_t pa = xv::phys(xv::thr_a(t));
+  XAcc<FIRST, VC> acc;
+#pragma unroll
+  for (int i = 0; i < XAcc<FIRST, VC>::N; ++i) acc.f[i] = {0.f, 0.f};
+  Cx<float> v[32];
+  uint64_t k = 0;
+  bool ok = true;
+  for (; k < nmine; ++k) {
+    const int st = (int)(k % XSTAGES);
+    const float2* xt = (const float2*)(buf + st * XTILE_BYTES);
+    const bool got = mbar_wait_or_abort(smem_u32(&full[st]), (uint32_t)((k / XSTAGES) & 1), abort_flag);
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const float4 q = *(const float4*)&xt[pa ^ xv::phys(xv::reg_a(2 * jj))];
+      v[2 * jj] = cx<float>(q.x, q.y);
+      v[2 * jj + 1] = cx<float>(q.z, q.w);
+    }
+    tile_views<FIRST, VC>(xt, v, acc, blockIdx.x + k * gridDim.x, tile_tot);
+    if (!bar_and(1, ETPB, got)) { ok = false; break; }   // also: the stage is free again
+    if (t == 0 && issued < nmine) issue();
+  }
+  if (!ok) {
+    if (t == 0) {
+      for (uint64_t kk = k; kk < issued; ++kk) mbar_wait(smem_u32(&full[kk % XSTAGES]), (uint32_t)((kk / XSTAGES) & 1));
+      atomicExch(err, 1);
+    }
+    return;
+  }
+  views_to_part<FIRST, VC>(acc, (double*)buf, part);
+}
+
+// adaptive 2-byte words: each thread loads its view-A words from global memory
+// and decodes them, the tile goes through shared memory for views C and B.
+template <bool FIRST, bool VC>
+__global__ void __launch_bounds__(ETPB, FIRST || VC ? 1 : 2) k_expect_ld(const unsigned int* __restrict__ s2,
+                                                        const __grid_constant__ XParams P,
+                                                        double* __restrict__ tile_tot, double* __restrict__ part,
+                                                        const A2Dev* __restrict__ a2) {
+  extern __shared__ __align__(16) float2 xt[];   // the tile, 2^13 complex64, swizzled
+  __shared__ Luts L;
+  build_luts(L, a2->r0, a2->r1);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t pa = xv::phys(xv::thr_a(t));
+  uint64_t woff = 0;
+  for (int k = 0; k < 5; ++k)
+    if ((lane >> k) & 1) woff |= 1ull << P.gpos[1 + k];
+  for (int k = 0; k < 3; ++k)
+    if ((warp >> k) & 1) woff |= 1ull << P.gpos[10 + k];
+  XAcc<FIRST, VC> acc;
+#pragma unroll
+  for (int i = 0; i < XAcc<FIRST, VC>::N; ++i) acc.f[i] = {0.f, 0.f};
+  const uint64_t ntiles = 1ull << (P.N - xv::TB);
+  Cx<float> v[32];
+  for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+    const uint64_t base = deposit(tau, P.out_mask) | woff;
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const unsigned int w = s2[(base + P.roff_a[jj]) >> 1];
+      v[2 * jj] = a2_dec(L, w & 0xFFFFu);
+      v[2 * jj + 1] = a2_dec(L, w >> 16);
+    }
+    __syncthreads();   // every view read of the previous tile is done
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj)
+      *(float4*)&xt[pa ^ xv::phys(xv::reg_a(2 * jj))] =
+          make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+    __syncthreads();
+    tile_views<FIRST, VC>(xt, v, acc, tau, tile_tot);
+  }
+  __syncthreads();
+  views_to_part<FIRST, VC>(acc, (double*)xt, part);
 }
 
 // ---- marginal -------------------------------------------------------------------------------
@@ -490,7 +725,7 @@ qs_status launch_norm(qs_sim* s, double* out) {
   return QS_OK;
 }
 
-template <typename R, int RB, int ENC>
+template <typename R, int RB>
 static qs_status expect_impl(qs_sim* s, double* qx, double* qy, double* qz) {
   const int N = s->N;
   const int b = RB + 8;
@@ -553,9 +788,8 @@ static qs_status expect_impl(qs_sim* s, double* qx, double* qy, double* qz) {
   QS_CUDA(cudaMemcpyAsync(sc + ql_off, ql, 64, cudaMemcpyHostToDevice, s->stream));
   for (int i = 0; i < np; ++i) {
     const size_t smem = 256 + SAcc<R>::bytes(nacc_of[i]) + 8 * sizeof(double);
-    QS_CUDA(cudaFuncSetAttribute(k_expect2<R, RB, ENC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_expect2<R, RB, ENC><<<grid, ETPB, smem, s->stream>>>(s->state, passes[i].P, sc + tt_off, sc + part_off[i],
-                                                           (const A2Dev*)s->a2dev);
+    QS_CUDA(cudaFuncSetAttribute(k_expect2<R, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_expect2<R, RB><<<grid, ETPB, smem, s->stream>>>(s->state, passes[i].P, sc + tt_off, sc + part_off[i]);
     QS_LAUNCH_CHECK();
     k_sum_columns<<<nacc_of[i], TPB, 0, s->stream>>>(sc + part_off[i], grid, nacc_of[i], sc + res_off[i]);
     QS_LAUNCH_CHECK();
@@ -589,6 +823,175 @@ static qs_status expect_impl(qs_sim* s, double* qx, double* qy, double* qz) {
   return QS_OK;
 }
 
+// Tensor map of one complex64 pass (see k_expect_tma): 5 dims of floats, the
+// box one 64 KB tile in the 128-byte swizzle.  Dims 1 and 2 are the tile's
+// two segments (f = 0: the run split 5 + 4), dims 3 and 4 the qubits below
+// and above the run.
+static qs_status expect_tensor_map(const qs_sim* s, const XParams& P, CUtensorMap* map) {
+  qs_tma::EncodeTiledFn enc = qs_tma::encode_fn();
+  if (!enc) {
+    qs_set_error("expect_xyz: cuTensorMapEncodeTiled is not available from the driver");
+    return QS_ECUDA;
+  }
+  const int N = s->N, f = P.f, b = P.b;
+  const cuuint64_t el = 8;   // bytes per amplitude
+  const int top = b + 9 - f;  // first qubit above the run
+  const cuuint64_t hi_stride = el << top;
+  const cuuint64_t lo_stride = el << (4 + f);
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5];
+  dims[0] = 32; box[0] = 32;
+  if (f == 0) {
+    dims[1] = 32; box[1] = 32; strides[0] = el << b;
+    dims[2] = 16; box[2] = 16; strides[1] = el << (b + 5);
+  } else {
+    dims[1] = 1ull << f; box[1] = 1u << f; strides[0] = el * 16;
+    dims[2] = 1ull << (9 - f); box[2] = 1u << (9 - f); strides[1] = el << b;
+  }
+  dims[3] = 1ull << P.lo_bits; box[3] = 1; strides[2] = P.lo_bits > 0 ? lo_stride : hi_stride;
+  dims[4] = 1ull << (N - top); box[4] = 1; strides[3] = hi_stride;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, s->state, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    qs_set_error("expect_xyz: cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return QS_ECUDA;
+  }
+  return QS_OK;
+}
+
+template <int ENC>
+static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz) {
+  const int N = s->N;
+  if (N < xv::TB) return QS_EUNSUPPORTED;
+  const uint64_t ntiles = 1ull << (N - xv::TB);
+  const int G = ENC == 0 ? s->num_sms : s->num_sms * 2;
+  const int grid = (int)(ntiles < (uint64_t)G ? ntiles : (uint64_t)G);
+  const uint64_t all = (N >= 64) ? ~0ull : ((1ull << N) - 1);
+  // pass 0: qubits 0..12; then qubits 13..N-1 in runs of near-equal length
+  // (the longer ones first), each run new in its pass
+  XParams ps[8];
+  int first_new[8];
+  int np = 0;
+  auto add_pass = [&](int f, int b) {
+    XParams& P = ps[np];
+    memset(&P, 0, sizeof P);
+    P.N = N; P.f = f; P.b = b; P.lo_bits = b - 4 - f;
+    first_new[np] = np == 0 ? 0 : b;
+    uint64_t tmask = 0;
+    for (int k = 0; k < xv::TB; ++k) {
+      P.gpos[k] = (uint8_t)(k < 4 + f ? k : b + (k - 4 - f));
+      tmask |= 1ull << P.gpos[k];
+    }
+    P.out_mask = all & ~tmask;
+    for (int jj = 0; jj < 16; ++jj) {
+      const uint32_t l = xv::reg_a(2 * jj);
+      uint64_t g = 0;
+      for (int k = 0; k < xv::TB; ++k)
+        if ((l >> k) & 1) g |= 1ull << P.gpos[k];
+      P.roff_a[jj] = g;
+    }
+    ++np;
+  };
+  add_pass(0, 4);
+  const int rem = N - xv::TB, nl = (rem + 8) / 9;
+  for (int p = 0, b = xv::TB; p < nl; ++p) {
+    const int len = rem / nl + (p < rem % nl ? 1 : 0);
+    add_pass(9 - len, b);
+    b += len;
+  }
+  // scratch: per pass partials and column sums, tile totals, outer-qubit P1,
+  // the error word
+  const int nq_out = N - xv::TB;
+  size_t off = 0;
+  size_t part_off[8], res_off[8];
+  for (int i = 0; i < np; ++i) {
+    part_off[i] = off; off += (size_t)grid * xv::NCOL;
+    res_off[i] = off; off += xv::NCOL;
+  }
+  const size_t tt_off = off; off += ntiles * 8;
+  const int gtb = 64;
+  const size_t tbp_off = off; off += (size_t)gtb * (nq_out + 1);
+  const size_t tbr_off = off; off += nq_out + 1;
+  const size_t ql_off = off; off += 8;    // 64 bytes of qubit list
+  const size_t err_off = off; off += 1;
+  QS_TRY(ensure_scratch(s, off * sizeof(double)));
+  double* sc = (double*)s->scratch;
+  // k_tile_bits: P1 of the qubits outside the pass-0 tile
+  RedParams rp;
+  memset(&rp, 0, sizeof rp);
+  rp.N = N;
+  rp.out_mask = ps[0].out_mask;
+  for (int k = 0; k < 3; ++k) rp.warp_g[k] = ps[0].gpos[10 + k];
+  uint8_t ql[64];
+  int nql = 0;
+  for (int q = 0; q < N; ++q)
+    if ((rp.out_mask >> q) & 1) ql[nql++] = (uint8_t)q;
+  QS_CUDA(cudaMemcpyAsync(sc + ql_off, ql, 64, cudaMemcpyHostToDevice, s->stream));
+  int* err = (int*)(sc + err_off);
+  QS_CUDA(cudaMemsetAsync(err, 0, sizeof(double), s->stream));
+  for (int i = 0; i < np; ++i) {
+    if (ENC == 0) {
+      CUtensorMap map;
+      QS_TRY(expect_tensor_map(s, ps[i], &map));
+      auto go = [&](auto kern) -> qs_status {
+        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XTMA_SMEM));
+        kern<<<grid, ETPB, XTMA_SMEM, s->stream>>>(map, ps[i], sc + tt_off, sc + part_off[i], err);
+        return QS_OK;
+      };
+      const bool vc = i == np - 1;
+      QS_TRY(i == 0 ? (vc ? go(k_expect_tma<true, true>) : go(k_expect_tma<true, false>))
+                    : (vc ? go(k_expect_tma<false, true>) : go(k_expect_tma<false, false>)));
+    } else {
+      const size_t smem = sizeof(float2) << xv::TB;
+      auto go = [&](auto kern) -> qs_status {
+        QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, ETPB, smem, s->stream>>>((const unsigned int*)s->state, ps[i], sc + tt_off, sc + part_off[i],
+                                              (const A2Dev*)s->a2dev);
+        return QS_OK;
+      };
+      const bool vc = i == np - 1;
+      QS_TRY(i == 0 ? (vc ? go(k_expect_ld<true, true>) : go(k_expect_ld<true, false>))
+                    : (vc ? go(k_expect_ld<false, true>) : go(k_expect_ld<false, false>)));
+    }
+    QS_LAUNCH_CHECK();
+    k_sum_columns<<<xv::NCOL, TPB, 0, s->stream>>>(sc + part_off[i], grid, xv::NCOL, sc + res_off[i]);
+    QS_LAUNCH_CHECK();
+  }
+  // the total and P1 of the qubits outside the pass-0 tile
+  k_tile_bits<<<gtb, TPB, 0, s->stream>>>(sc + tt_off, ntiles, rp, nql, (const uint8_t*)(sc + ql_off), sc + tbp_off);
+  QS_LAUNCH_CHECK();
+  k_sum_columns<<<nql + 1, TPB, 0, s->stream>>>(sc + tbp_off, gtb, nql + 1, sc + tbr_off);
+  QS_LAUNCH_CHECK();
+  QS_TRY(ensure_hbuf(s, off * sizeof(double)));
+  QS_CUDA(cudaMemcpyAsync(s->hbuf, sc, off * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(cudaStreamSynchronize(s->stream));
+  const double* h = (const double*)s->hbuf;
+  if (*(const int*)(h + err_off)) {
+    qs_set_error("expect_xyz: a tensor-load wait ran out of time");
+    return QS_ETIMEOUT;
+  }
+  const double nrm = h[tbr_off];
+  for (int i = 0; i < nql; ++i) qz[ql[i]] = h[tbr_off + i + 1];
+  // each qubit once: views A and B of pass 0 and the new qubits of views A
+  // and B of the later passes; view C (qubits 1..3) of the last pass
+  const uint8_t* regs[3] = {xv::REG_A, xv::REG_B, xv::REG_C};
+  for (int i = 0; i < np; ++i)
+    for (int k = 0; k < xv::NVIEW; ++k) {
+      if (k == 2 && i != np - 1) continue;
+      for (int sl = 0; sl < (k == 2 ? 3 : 5); ++sl) {
+        const int q = ps[i].gpos[regs[k][sl]];
+        if (k < 2 && q < first_new[i]) continue;
+        const double* c = h + res_off[i] + k * xv::NV;
+        qx[q] = 0.5 * nrm - c[2 * sl];
+        qy[q] = 0.5 * nrm - c[2 * sl + 1];
+        if (i == 0 || k == 2) qz[q] = c[10 + sl];
+      }
+    }
+  return QS_OK;
+}
+
 static qs_status expect_small(qs_sim* s, double* qx, double* qy, double* qz) {
   if (s->N > 12) return QS_EUNSUPPORTED;
   QS_TRY(ensure_scratch(s, sizeof(double) * (1 + 3 * s->N)));
@@ -610,9 +1013,9 @@ static qs_status expect_small(qs_sim* s, double* qx, double* qy, double* qz) {
 }
 
 qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz) {
-  if (s->enc == QS_C128 && s->N >= 12) return expect_impl<double, 4, 1>(s, qx, qy, qz);
-  if (s->enc == QS_C64 && s->N >= 13) return expect_impl<float, 5, 0>(s, qx, qy, qz);
-  if (s->enc == QS_ADAPT2 && s->N >= 13) return expect_impl<float, 5, 2>(s, qx, qy, qz);
+  if (s->enc == QS_C128 && s->N >= 12) return expect_impl<double, 4>(s, qx, qy, qz);
+  if (s->enc == QS_C64 && s->N >= 13) return expect_views_impl<0>(s, qx, qy, qz);
+  if (s->enc == QS_ADAPT2 && s->N >= 13) return expect_views_impl<2>(s, qx, qy, qz);
   return expect_small(s, qx, qy, qz);
 }
 

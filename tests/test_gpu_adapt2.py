@@ -163,7 +163,7 @@ def test_permutation_and_shorbox_bit_exact(q):
         assert r == (ref.r0, ref.r1)
 
 
-@pytest.mark.parametrize("N", [5, 13, 16])
+@pytest.mark.parametrize("N", [5, 13, 16, 23])
 def test_reductions(q, N):
     a = rand_astate(N, 99)
     z = a.to_complex()

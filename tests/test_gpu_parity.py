@@ -167,7 +167,7 @@ def test_layered_circuit_n20(q, enc):
 
 
 @pytest.mark.parametrize("enc", ["c128", "c64"])
-@pytest.mark.parametrize("N", [2, 4, 9, 12, 13, 14, 17, 22])
+@pytest.mark.parametrize("N", [2, 4, 9, 12, 13, 14, 17, 22, 23])
 def test_reductions(q, enc, N):
     v0 = rand_state(N, 5 * N) * 0.97
     with q.Sim(N, enc) as s:
