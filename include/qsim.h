@@ -257,7 +257,11 @@ qs_status sim_norm(qs_sim* sim, double* out);
  * qx[n] = <(1 - sigma^x_n)>/2, qy[n] = <(1 - sigma^y_n)>/2,
  * qz[n] = <(1 - sigma^z_n)>/2, i.e. with w_n = sum_{bit n = 0} conj(a_i) a_{i+2^n}:
  * qx = <Phi|Phi>/2 - Re w_n, qy = <Phi|Phi>/2 - Im w_n, qz = P(qubit n = 1).
- * qx, qy, qz: host arrays of N doubles.  The state is unchanged. */
+ * qx, qy, qz: host arrays of N doubles.  The state is unchanged.  Sums are
+ * FP64 in a fixed order (FP32 leaf sums of at most 16 pairs per thread and
+ * tile for complex64 and the adaptive words).  Returns QS_ETIMEOUT (outputs
+ * undefined, the state unchanged) if a bounded wait of the complex64 kernel
+ * for its tensor loads ran out. */
 qs_status expect_xyz(qs_sim* sim, double* qx, double* qy, double* qz);
 
 /* Marginal distribution of the nq qubits `qubits` (Sec. 2: the probability
