@@ -47,12 +47,26 @@ UNIT = "updates/s"
 # which the first only writes, scaled by the 16x units
 # (profiles/tile_pass_c64_n26_traffic.md); None when a pass kernel changes
 # after the capture
-TILE_TRAFFIC_PER_PASS = 1.5566e10
+TILE_TRAFFIC_PER_PASS = 1.5326e10
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
     from paper_1805_04708_gb300 import workloads as wl
     return wl.random_gate_circuit(N, ngates, seed)
+
+
+def product_start_gates(recs):
+    """Gates of a run from |0..0> that the library composes into the product
+    start (sim_set_product_start): single-qubit gates that precede every
+    multi-qubit gate on their qubit."""
+    entangled, n = set(), 0
+    for r in recs:
+        qs = r[1]
+        if len(qs) == 1 and qs[0] not in entangled:
+            n += 1
+        elif len(qs) > 1:
+            entangled.update(qs)
+    return n
 
 
 TILE_MODES = {1: "op interpreter k_tile2",
@@ -236,6 +250,14 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
         if m != 1:
             qsim.circuit_compile(N, gates, mode=m)
         v["c64_tile_mode%d" % m] = dict(tile_mode(m), kernels=TILE_MODES[m])
+    # the same circuit with every gate in the passes (no product start); in
+    # mode 2 the new pass structures take 4 runs to tune
+    sim.set_product_start(False)
+    for _ in range(4 if mode == 2 else 0):
+        sim.reset()
+        sim.circuit_run(gates, mode=mode)
+    v["c64_tile_mode%d_no_product_start" % mode] = dict(tile_mode(mode), kernels=TILE_MODES[mode])
+    sim.set_product_start(True)
 
     def per_gate_c64():
         sim.reset()
@@ -501,7 +523,9 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 arithmetic, f64 reductions)",
         "data": "synthetic", "config": dict(config_dict(N, "c64"), parallelism="replicas" if world > 1 else "single"),
         "path": {"tile_passes": "circuit_run mode %d: %s" % (mode, TILE_MODES[mode]),
-                 "pass_compile_s": round(t_compile, 3)},
+                 "pass_compile_s": round(t_compile, 3),
+                 "product_start_gates": product_start_gates(recs),
+                 "passes_per_step": passes_per_step},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "variants": variants,
     }

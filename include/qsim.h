@@ -118,6 +118,17 @@ qs_status sim_reset(qs_sim* sim);
  * counterpart. */
 qs_status sim_set_lazy_reset(qs_sim* sim, int on);
 
+/* Product start (on: nonzero; default on).  When circuit_run (modes 1-3) of a
+ * complex64 state starts from a pending |0..0>, every single-qubit gate that
+ * comes before all multi-qubit gates on its qubit acts on an unentangled
+ * qubit and commutes with every earlier gate on other qubits; these gates are
+ * composed per qubit (FP64) and the first tile pass writes the product state
+ * prod_q (U_q |0>)(bit q) instead of applying them one by one.  The result
+ * equals the gate-by-gate one up to rounding.  Off: every gate runs in the
+ * passes.  The paper has no counterpart (its runs start from a written
+ * state). */
+qs_status sim_set_product_start(qs_sim* sim, int on);
+
 /* ---- gates (Sec. 2, Eq. (NUM2); Appendix A) ------------------------------ */
 /* Single-qubit gate: for every basis index i with bit `target` = 0,
  * (a_i, a_{i+2^target}) <- U (a_i, a_{i+2^target}) (Eq. (NUM2), Eq. (AQS0)).

@@ -29,6 +29,8 @@ struct qs_sim {
                       // tile pass makes its tiles instead of loading them,
                       // every other call that touches the amplitudes writes
                       // them first
+  bool product_start; // complex64 tile runs from a pending |0..0> start from
+                      // the product state of their leading single-qubit gates
 };
 // Write a pending |0..0> (no-op otherwise).
 qs_status materialize_state(qs_sim* s);

@@ -438,7 +438,71 @@ struct PassSink {
   std::vector<JitJob>* collect;   // compile only: the kernels to compile
   std::vector<int>* plan;         // plan only: gate indices in run order
   std::vector<int>* plan_start;   // plan only: first index of each pass
+  const double (*prod)[2][2];     // complex64 run from a pending |0..0>: the
+                                  // product start f[q][bit] = (re, im), or null
 };
+
+// Product start.  From |0..0>, a single-qubit gate that comes before every
+// multi-qubit gate on its qubit acts on an unentangled qubit: it commutes
+// with every earlier gate of other qubits, so these gates can all run first,
+// and together they make the product state prod_q (U_q |0>)_(bit q), U_q the
+// product of qubit q's gates in order.  Returns their number; f[q][bit] gets
+// (U_q |0>)(bit) (FP64), rest the other gates in order.
+static int product_prefix(int N, const qs_gate* g, int n, double (*f)[2][2], std::vector<qs_gate>* rest) {
+  for (int q = 0; q < N; ++q) {
+    f[q][0][0] = 1.0; f[q][0][1] = 0.0;
+    f[q][1][0] = 0.0; f[q][1][1] = 0.0;
+  }
+  rest->clear();
+  uint64_t entangled = 0;
+  int np = 0;
+  for (int i = 0; i < n; ++i) {
+    const qs_gate& x = g[i];
+    if (x.nc == 0 && !((entangled >> x.target) & 1)) {
+      double* v = &f[x.target][0][0];   // v[0..1] = f(0), v[2..3] = f(1)
+      const double* u = x.u;            // u00, u01, u10, u11
+      const double a0r = v[0], a0i = v[1], a1r = v[2], a1i = v[3];
+      v[0] = u[0] * a0r - u[1] * a0i + u[2] * a1r - u[3] * a1i;
+      v[1] = u[0] * a0i + u[1] * a0r + u[2] * a1i + u[3] * a1r;
+      v[2] = u[4] * a0r - u[5] * a0i + u[6] * a1r - u[7] * a1i;
+      v[3] = u[4] * a0i + u[5] * a0r + u[6] * a1i + u[7] * a1r;
+      ++np;
+      continue;
+    }
+    entangled |= 1ull << x.target;
+    for (int c = 0; c < x.nc; ++c) entangled |= 1ull << x.controls[c];
+    rest->push_back(x);
+  }
+  return np;
+}
+
+static uint64_t f2_bits_host(double re, double im) {
+  const float fr = (float)re, fi = (float)im;
+  uint32_t br, bi;
+  memcpy(&br, &fr, 4);
+  memcpy(&bi, &fi, 4);
+  return (uint64_t)br | ((uint64_t)bi << 32);
+}
+
+// The product start of a complex64 pass: per-qubit factors and the register
+// table of the load map (products in FP64, rounded once).
+static void fill_product(TileParams2& P, const double (*f)[2][2], int RB) {
+  P.from_product = 1;
+  for (int q = 0; q < P.N; ++q)
+    for (int bit = 0; bit < 2; ++bit) P.pf[q][bit] = f2_bits_host(f[q][bit][0], f[q][bit][1]);
+  for (int j = 0; j < (1 << RB); ++j) {
+    double tr = 1.0, ti = 0.0;
+    for (int sl = 0; sl < RB; ++sl) {
+      const int l = P.init.reg[sl];
+      const int q = l < LOW_BITS ? l : P.gpos[l];
+      const double* c = f[q][(j >> sl) & 1];
+      const double r = tr * c[0] - ti * c[1];
+      ti = tr * c[1] + ti * c[0];
+      tr = r;
+    }
+    P.ptab[j] = f2_bits_host(tr, ti);
+  }
+}
 
 static qs_status emit_pass(PassSink& k, const TileParams2& P);
 
@@ -520,8 +584,14 @@ static qs_status plan_tile_passes(PassSink& k, const qs_gate* gates, int n) {
   return st;
 }
 
+// A circuit that is all product start still needs one pass to write it.
+static qs_status run_empty_pass(PassSink& k) {
+  const int b = tile_bits(k.enc);
+  return run_pass(k, nullptr, nullptr, 0, (1ull << b) - 1);
+}
+
 qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes, PassTimer* timer, int jit) {
-  PassSink k = {s, s->N, s->enc, 0, timer, 0, nullptr, nullptr, nullptr};
+  PassSink k = {s, s->N, s->enc, 0, timer, 0, nullptr, nullptr, nullptr, nullptr};
   if (s->enc == QS_C64 && jit != 0) {
     if (!tile_jit_available()) {
       qs_set_error("circuit_run: compiled tile passes need NVRTC, which could not be loaded");
@@ -529,23 +599,39 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
     }
     k.jit = jit;
   }
-  const qs_status st = plan_tile_passes(k, gates, n);
+  qs_status st;
+  static thread_local double prod[64][2][2];
+  static thread_local std::vector<qs_gate> rest;
+  if (s->enc == QS_C64 && s->zero_pending && s->product_start &&
+      product_prefix(s->N, gates, n, prod, &rest) > 0) {
+    k.prod = prod;
+    st = rest.empty() ? run_empty_pass(k) : plan_tile_passes(k, rest.data(), (int)rest.size());
+  } else {
+    st = plan_tile_passes(k, gates, n);
+  }
   if (n_passes) *n_passes = k.emitted;
   return st;
 }
 
 qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes) {
   std::vector<JitJob> passes;
-  PassSink k = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes, nullptr, nullptr};
+  PassSink k = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes, nullptr, nullptr, nullptr};
   QS_TRY(plan_tile_passes(k, gates, n));
   if (n_passes) *n_passes = k.emitted;
+  // the passes of a run from a pending |0..0> (the gates after the product start)
+  std::vector<qs_gate> rest;
+  static thread_local double prod[64][2][2];
+  if (product_prefix(N, gates, n, prod, &rest) > 0) {
+    PassSink kz = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes, nullptr, nullptr, nullptr};
+    QS_TRY(rest.empty() ? run_empty_pass(kz) : plan_tile_passes(kz, rest.data(), (int)rest.size()));
+  }
   return tile_jit_compile_all(passes);
 }
 
 qs_status plan_tile_pass_order(int N, qs_encoding enc, const qs_gate* gates, int n, int* order, int* pass_start,
                                int* n_passes) {
   std::vector<int> plan, start;
-  PassSink k = {nullptr, N, enc, 0, nullptr, 0, nullptr, &plan, &start};
+  PassSink k = {nullptr, N, enc, 0, nullptr, 0, nullptr, &plan, &start, nullptr};
   QS_TRY(plan_tile_passes(k, gates, n));
   for (size_t i = 0; i < plan.size(); ++i) order[i] = plan[i];
   for (size_t i = 0; i < start.size(); ++i) pass_start[i] = start[i];
@@ -636,8 +722,11 @@ static qs_status run_pass(PassSink& k, const qs_gate* gates, const int* gidx, in
     return QS_OK;
   }
   if (build_pass(gates, gidx, ng, k.N, b, tile_register_bits(k.enc), tile, &P, k.enc == QS_C64)) {
-    // a pending |0..0> is made by the first pass instead of being loaded
+    // a pending |0..0> (or the product start) is made by the first pass
+    // instead of being loaded
     P.from_zero = (k.s && k.s->zero_pending) ? 1 : 0;
+    P.from_product = 0;
+    if (P.from_zero && k.prod) fill_product(P, k.prod, tile_register_bits(k.enc));
     QS_TRY(emit_pass(k, P));
     if (P.from_zero) k.s->zero_pending = false;
     return QS_OK;

@@ -66,6 +66,13 @@ struct TileParams2 {
   int last_xpose;      // index of the last transpose op, -1 if none
   int from_zero;       // the state is |0..0> and not in memory: tiles start as
                        // zeros (amplitude 1 at index 0), nothing is loaded
+  // complex64, with from_zero: tiles start as the product state
+  // a(i) = prod_q f_q(bit q of i) instead (f_q = (1, 0) for every q is |0..0>).
+  // pf[q][bit]: f_q(bit) as float2 bits; ptab[j]: the product over the
+  // register slots of the load map for register j, formed in FP64
+  int from_product;
+  uint64_t pf[64][2];
+  uint64_t ptab[32];
   TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
   TMap maps[16];
   // T_DIAG_TAB: the factor of register j, complex64 (re, im) float bits in
@@ -329,6 +336,15 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// complex64 product-start helpers
+__device__ __forceinline__ Cx<float> f2_bits(uint64_t u) {
+  return cx<float>(__uint_as_float((unsigned)(u & 0xFFFFFFFFu)), __uint_as_float((unsigned)(u >> 32)));
+}
+__device__ __forceinline__ Cx<float> pf_at(const TileParams2& P, int q, int bit) { return f2_bits(P.pf[q][bit]); }
+__device__ __forceinline__ Cx<float> cmul_f(Cx<float> a, Cx<float> b) {
+  return cx<float>(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
 // Each thread stages exactly the 16-byte chunks it will read back, so the
 // stage buffer needs no barrier: the thread's own wait_group orders it.
 template <typename R, int RB>
@@ -391,12 +407,37 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
   const uint64_t ntiles = 1ull << (P.N - P.b);
   Cx<R> v[NR];
   const bool load = !P.from_zero;
+  // product start: the factor of this thread's lane and warp bits
+  Cx<float> fthr = cx<float>(1.f, 0.f);
+  if (sizeof(R) == 4 && P.from_product) {
+    for (int k = 1; k < P.b; ++k) {
+      bool is_reg = false;
+#pragma unroll
+      for (int sl = 0; sl < RB; ++sl) is_reg |= (P.init.reg[sl] == k);
+      if (is_reg) continue;
+      const int q = k < 4 ? k : P.gpos[k];
+      fthr = cmul_f(fthr, pf_at(P, q, (tl_in >> k) & 1));
+    }
+  }
   if (load && blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
     const uint64_t base = deposit_t(tau, P.out_mask);
     if (load) {
       cp_async_wait_all();
       unstage_tile<R, RB>(stg, v, P.init, tl_in);
+    } else if (sizeof(R) == 4 && P.from_product) {
+      // product state: thread factor x the factors of the qubits outside the
+      // tile x the register table
+      Cx<float> f = fthr;
+      for (uint64_t m = P.out_mask; m; m &= m - 1) {
+        const int q = __ffsll((long long)m) - 1;
+        f = cmul_f(f, pf_at(P, q, (int)((base >> q) & 1)));
+      }
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const Cx<float> t = cmul_f(f, f2_bits(P.ptab[j]));
+        v[j] = cx<R>((R)t.x, (R)t.y);
+      }
     } else {
       // |0..0>: register 0 of thread 0 of the tile at base 0 is index 0
 #pragma unroll

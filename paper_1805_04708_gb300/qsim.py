@@ -74,6 +74,7 @@ _SIGS = {
     "sim_info": (_I, [_P, _IP, _IP, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
     "sim_reset": (_I, [_P]),
     "sim_set_lazy_reset": (_I, [_P, _I]),
+    "sim_set_product_start": (_I, [_P, _I]),
     "apply_gate": (_I, [_P, _I, _D]),
     "apply_controlled": (_I, [_P, _IP, _I, _I, _D]),
     "apply_fused": (_I, [_P, _IP, _I, _D]),
@@ -241,8 +242,9 @@ class Sim:
         _check(_lib.sim_create_in(self.N, self.enc, _P(ptr_al), avail, _P(self.stream_handle), ctypes.byref(h)))
         self._h = h
         self.nbytes = nbytes
-        if own:   # the buffer is private: resets may stay pending
+        if own:   # the buffer is private: resets may stay pending, from the start
             _check(_lib.sim_set_lazy_reset(h, 1))
+            _check(_lib.sim_reset(h))
 
     # -- lifetime --
     def close(self):
@@ -298,6 +300,11 @@ class Sim:
         """Kernel family for apply_fused on complex64 states: "auto" (tcgen05
         where the gate qualifies), "cuda_cores" or "mma_sync"."""
         _check(_lib.sim_set_fused_engine(self._h, self.FUSED_ENGINES[engine]))
+
+    def set_product_start(self, on=True):
+        """Product start of complex64 tile runs from a pending |0..0> (see
+        sim_set_product_start); on by default."""
+        _check(_lib.sim_set_product_start(self._h, 1 if on else 0))
 
     def apply_permutation(self, controls, reg_lo, reg_w, table):
         c, nc = _ints(controls)
