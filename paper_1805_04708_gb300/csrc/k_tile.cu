@@ -550,6 +550,25 @@ static qs_status plan_tile_passes(PassSink& k, const qs_gate* gates, int n) {
   // high targets as the lanes and register slots hold (no transposes); the
   // warp bits are padding.
   const int max_targets = LOW_BITS + 2 + (tile_register_bits(k.enc) - 1);
+  // tile of a pass: its targets, padded to b bits with qubits the pass does
+  // not touch at all (diagonal gates and controls on qubits outside the tile
+  // are per-tile constants, a diagonal folds into one factor; inside it they
+  // cost per-element work)
+  auto tile_of = [&](const std::vector<int>& g) {
+    uint64_t S = low, used = 0;
+    for (int i : g) { S |= xq[i]; used |= xq[i] | zq[i]; }
+    uint64_t tile = S;
+    for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q)
+      if (!((used >> q) & 1)) tile |= 1ull << q;
+    for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
+    return tile;
+  };
+  auto targets_of = [&](const std::vector<int>& g) {
+    uint64_t S = low;
+    for (int i : g) S |= xq[i];
+    return S;
+  };
+  std::vector<std::vector<int>> passes;
   qs_status st = QS_OK;
   while (nrem > 0 && st == QS_OK) {
     uint64_t S = low, bx = 0, bz = 0;
@@ -568,18 +587,21 @@ static qs_status plan_tile_passes(PassSink& k, const qs_gate* gates, int n) {
       }
     }
     nrem = nleft;
-    // pad the tile to b bits with qubits the pass does not touch at all:
-    // diagonal gates and controls on qubits outside the tile are per-tile
-    // constants (a diagonal folds into one factor), inside it they cost
-    // per-element work
-    uint64_t used = 0;
-    for (int j = 0; j < ng; ++j) used |= xq[gidx[j]] | zq[gidx[j]];
-    uint64_t tile = S;
-    for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q)
-      if (!((used >> q) & 1)) tile |= 1ull << q;
-    for (int q = 0; q < N && __builtin_popcountll(tile) < b; ++q) tile |= 1ull << q;
-    st = run_pass(k, gates, gidx, ng, tile);
+    passes.emplace_back(gidx, gidx + ng);
   }
+  // A last pass of a few gates costs a whole sweep; when its targets and the
+  // previous pass's fit the tile, the previous pass takes its gates after
+  // its own (the same order) and reaches the extra targets through the warp
+  // bits by shared-memory transposes (about a third of a sweep each).
+  const size_t np = passes.size();
+  if (k.enc == QS_C64 && np >= 2 && passes[np - 1].size() <= 4 &&
+      passes[np - 2].size() + passes[np - 1].size() <= MAX_TOPS / 2 &&
+      __builtin_popcountll(targets_of(passes[np - 2]) | targets_of(passes[np - 1])) <= b) {
+    passes[np - 2].insert(passes[np - 2].end(), passes[np - 1].begin(), passes[np - 1].end());
+    passes.pop_back();
+  }
+  for (size_t p = 0; p < passes.size() && st == QS_OK; ++p)
+    st = run_pass(k, gates, passes[p].data(), (int)passes[p].size(), tile_of(passes[p]));
   free(gidx); free(rem); free(xq); free(zq);
   return st;
 }
