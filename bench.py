@@ -47,7 +47,7 @@ UNIT = "updates/s"
 # which the first only writes, scaled by the 16x units
 # (profiles/tile_pass_c64_n26_traffic.md); None when a pass kernel changes
 # after the capture
-TILE_TRAFFIC_PER_PASS = 1.5326e10
+TILE_TRAFFIC_PER_PASS = 1.5232e10
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
