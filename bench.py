@@ -447,8 +447,7 @@ def run_gpu(args):
         ms = sim.circuit_run_timed(gates, mode=mode)
         if timed_passes is not None:
             timed_passes.extend(ms)
-        sim.norm()
-        sim.expect_xyz()
+        sim.expect_xyz_norm()
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -502,8 +501,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         sim.reset()
         sim.circuit_run(recs, mode=mode)
-        sim.norm()
-        sim.expect_xyz()
+        sim.expect_xyz_norm()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": world * upd_per_step / e2e_s, "unit": UNIT,

@@ -275,6 +275,12 @@ qs_status sim_norm(qs_sim* sim, double* out);
  * for its tensor loads ran out. */
 qs_status expect_xyz(qs_sim* sim, double* qx, double* qy, double* qz);
 
+/* expect_xyz and sim_norm in one call: the same values (norm: sim_norm's
+ * exact-product, compensated sum), from fewer sweeps of the state where the
+ * kernels allow (complex64, N >= 23: one BEGIN MEASUREMENT pass also sums
+ * |a|^2).  norm: host, one double.  Errors as expect_xyz. */
+qs_status expect_xyz_norm(qs_sim* sim, double* qx, double* qy, double* qz, double* norm);
+
 /* Marginal distribution of the nq qubits `qubits` (Sec. 2: the probability
  * of outcome 0/1 for a single qubit, generalised to a register):
  * out[k] = sum over basis states whose qubit qubits[m] equals bit m of k of

@@ -441,6 +441,13 @@ extern "C" qs_status expect_xyz(qs_sim* s, double* qx, double* qy, double* qz) {
   return launch_expect(s, qx, qy, qz);
 }
 
+extern "C" qs_status expect_xyz_norm(qs_sim* s, double* qx, double* qy, double* qz, double* norm) {
+  QS_TRY(check_sim(s));
+  CHECK_ARG(qx && qy && qz && norm, "expect_xyz_norm: null output");
+  QS_TRY(materialize_state(s));
+  return launch_expect_norm(s, qx, qy, qz, norm);
+}
+
 extern "C" qs_status measure_probs(qs_sim* s, const int* qubits, int nq, double* out) {
   QS_TRY(check_sim(s));
   CHECK_ARG(nq >= 1 && nq <= 24 && nq <= s->N, "measure_probs: nq = %d not in 1..min(24, N)", nq);

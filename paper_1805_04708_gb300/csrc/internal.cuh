@@ -102,6 +102,7 @@ qs_status launch_reset(qs_sim* s);
 // Reductions (all encodings); results on the host.
 qs_status launch_norm(qs_sim* s, double* out);
 qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz);
+qs_status launch_expect_norm(qs_sim* s, double* qx, double* qy, double* qz, double* norm);
 qs_status launch_marginal(qs_sim* s, const int* qubits, int nq, double* out);
 
 // Tile passes --------------------------------------------------------------------

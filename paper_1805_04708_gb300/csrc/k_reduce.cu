@@ -419,16 +419,21 @@ struct XParams {
 // of their 5 register slots (and in the first pass P1 of each slot), view C
 // (VC: the last pass, whose ALU load is lighter) w and P1 of its slots 0..2,
 // qubits 1..3, which every tile holds.
-template <bool FIRST, bool VC>
+// NORM: one more accumulator, sum |a|^2 from exact products (column 15).
+template <bool FIRST, bool VC, bool NORM = false>
 struct XAcc {
-  static constexpr int NA = FIRST ? 15 : 10, NC = VC ? 9 : 0, N = 2 * NA + NC;
+  static constexpr int NA = FIRST ? 15 : 10, NC = VC ? 9 : 0, N = 2 * NA + NC + (NORM ? 1 : 0);
   FF f[N];
   // output column of accumulator i (16 columns per view: w re/im of slot s at
-  // 2s, 2s+1, P1 of slot s at 10+s)
+  // 2s, 2s+1, P1 of slot s at 10+s; the norm at 15)
   __host__ __device__ static constexpr int col(int i) {
-    return i < NA ? i : i < 2 * NA ? xv::NV + (i - NA) : 2 * xv::NV + (i - 2 * NA < 6 ? i - 2 * NA : 4 + (i - 2 * NA));
+    return i < NA ? i
+           : i < 2 * NA ? xv::NV + (i - NA)
+           : i < 2 * NA + NC ? 2 * xv::NV + (i - 2 * NA < 6 ? i - 2 * NA : 4 + (i - 2 * NA))
+                             : xv::NV - 1;
   }
 };
+constexpr int XNORM_COL = xv::NV - 1;
 
 // Fold one view's per-thread leaf sums (FP32, at most 16 pairs each) into
 // acc[0 .. 2NS-1] (w re/im of slots 0..NS-1) and, with P1, acc[2NS ..
@@ -465,11 +470,16 @@ __device__ __forceinline__ void view_fold(const Cx<float>* v, FF* acc, float& T)
 
 // View A is in v; folds it, then views C (VC) and B read from the shared
 // tile xt.  FIRST also writes the per-(tile, warp) total of |a|^2.
-template <bool FIRST, bool VC>
-__device__ __forceinline__ void tile_views(const float2* xt, Cx<float> (&v)[32], XAcc<FIRST, VC>& acc, uint64_t tau,
-                                           double* __restrict__ tile_tot) {
+template <bool FIRST, bool VC, bool NORM>
+__device__ __forceinline__ void tile_views(const float2* xt, Cx<float> (&v)[32], XAcc<FIRST, VC, NORM>& acc,
+                                           uint64_t tau, double* __restrict__ tile_tot) {
   const int t = threadIdx.x;
-  constexpr int NA = XAcc<FIRST, VC>::NA;
+  constexpr int NA = XAcc<FIRST, VC, NORM>::NA;
+  if constexpr (NORM) {   // sum |a|^2 of view A's registers, products exact
+    FF& f = acc.f[XAcc<FIRST, VC, NORM>::N - 1];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { ff_add_prod(f, v[j].x, v[j].x); ff_add_prod(f, v[j].y, v[j].y); }
+  }
   float T;
   view_fold<5, FIRST>(v, acc.f, T);
   if (FIRST) {
@@ -497,10 +507,11 @@ __device__ __forceinline__ void tile_views(const float2* xt, Cx<float> (&v)[32],
 // CTA sum of the accumulators in FP64 in a fixed order (warp tree, then the 8
 // warps in order) into part[block][column]; red: XAcc::N * 8 doubles of
 // shared memory.  Columns no accumulator maps to are written as 0.
-template <bool FIRST, bool VC>
-__device__ __forceinline__ void views_to_part(const XAcc<FIRST, VC>& acc, double* red, double* __restrict__ part) {
+template <bool FIRST, bool VC, bool NORM>
+__device__ __forceinline__ void views_to_part(const XAcc<FIRST, VC, NORM>& acc, double* red,
+                                              double* __restrict__ part) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  constexpr int M = XAcc<FIRST, VC>::N;
+  constexpr int M = XAcc<FIRST, VC, NORM>::N;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const double d = warp_sum((double)acc.f[i].hi + (double)acc.f[i].lo);
@@ -512,7 +523,7 @@ __device__ __forceinline__ void views_to_part(const XAcc<FIRST, VC>& acc, double
   if (t < M) {
     double sum = 0.0;
     for (int w = 0; w < 8; ++w) sum += red[t * 8 + w];
-    part[(size_t)blockIdx.x * xv::NCOL + XAcc<FIRST, VC>::col(t)] = sum;
+    part[(size_t)blockIdx.x * xv::NCOL + XAcc<FIRST, VC, NORM>::col(t)] = sum;
   }
 }
 
@@ -527,7 +538,7 @@ constexpr int XSTAGES = 3;
 constexpr uint32_t XTILE_BYTES = 8u << xv::TB;
 constexpr size_t XTMA_SMEM = (size_t)XSTAGES * XTILE_BYTES + 1024 + 64;
 
-template <bool FIRST, bool VC>
+template <bool FIRST, bool VC, bool NORM>
 __global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ CUtensorMap map,
                                                          const __grid_constant__ XParams P,
                                                          double* __restrict__ tile_tot, double* __restrict__ part,
@@ -561,9 +572,9 @@ __global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ 
   if (t == 0)
     while (issued < nmine && issued < (uint64_t)XSTAGES) issue();
   const uint32_t pa = xv::phys(xv::thr_a(t));
-  XAcc<FIRST, VC> acc;
+  XAcc<FIRST, VC, NORM> acc;
 #pragma unroll
-  for (int i = 0; i < XAcc<FIRST, VC>::N; ++i) acc.f[i] = {0.f, 0.f};
+  for (int i = 0; i < XAcc<FIRST, VC, NORM>::N; ++i) acc.f[i] = {0.f, 0.f};
   Cx<float> v[32];
   uint64_t k = 0;
   bool ok = true;
@@ -577,7 +588,7 @@ __global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ 
       v[2 * jj] = cx<float>(q.x, q.y);
       v[2 * jj + 1] = cx<float>(q.z, q.w);
     }
-    tile_views<FIRST, VC>(xt, v, acc, blockIdx.x + k * gridDim.x, tile_tot);
+    tile_views<FIRST, VC, NORM>(xt, v, acc, blockIdx.x + k * gridDim.x, tile_tot);
     if (!bar_and(1, ETPB, got)) { ok = false; break; }   // also: the stage is free again
     if (t == 0 && issued < nmine) issue();
   }
@@ -588,7 +599,7 @@ __global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ 
     }
     return;
   }
-  views_to_part<FIRST, VC>(acc, (double*)buf, part);
+  views_to_part<FIRST, VC, NORM>(acc, (double*)buf, part);
 }
 
 // adaptive 2-byte words: each thread loads its view-A words from global memory
@@ -608,9 +619,9 @@ __global__ void __launch_bounds__(ETPB, FIRST || VC ? 1 : 2) k_expect_ld(const u
     if ((lane >> k) & 1) woff |= 1ull << P.gpos[1 + k];
   for (int k = 0; k < 3; ++k)
     if ((warp >> k) & 1) woff |= 1ull << P.gpos[10 + k];
-  XAcc<FIRST, VC> acc;
+  XAcc<FIRST, VC, false> acc;
 #pragma unroll
-  for (int i = 0; i < XAcc<FIRST, VC>::N; ++i) acc.f[i] = {0.f, 0.f};
+  for (int i = 0; i < XAcc<FIRST, VC, false>::N; ++i) acc.f[i] = {0.f, 0.f};
   const uint64_t ntiles = 1ull << (P.N - xv::TB);
   Cx<float> v[32];
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
@@ -627,10 +638,10 @@ __global__ void __launch_bounds__(ETPB, FIRST || VC ? 1 : 2) k_expect_ld(const u
       *(float4*)&xt[pa ^ xv::phys(xv::reg_a(2 * jj))] =
           make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
     __syncthreads();
-    tile_views<FIRST, VC>(xt, v, acc, tau, tile_tot);
+    tile_views<FIRST, VC, false>(xt, v, acc, tau, tile_tot);
   }
   __syncthreads();
-  views_to_part<FIRST, VC>(acc, (double*)xt, part);
+  views_to_part<FIRST, VC, false>(acc, (double*)xt, part);
 }
 
 // ---- marginal -------------------------------------------------------------------------------
@@ -861,8 +872,11 @@ static qs_status expect_tensor_map(const qs_sim* s, const XParams& P, CUtensorMa
   return QS_OK;
 }
 
+// norm_out (complex64 with a pass that has neither P1 nor view C, N >= 23):
+// that pass also sums |a|^2 from exact products; else null or not filled.
 template <int ENC>
-static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz) {
+static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz, double* norm_out,
+                                   bool* norm_done) {
   const int N = s->N;
   if (N < xv::TB) return QS_EUNSUPPORTED;
   const uint64_t ntiles = 1ull << (N - xv::TB);
@@ -931,6 +945,9 @@ static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz
   QS_CUDA(cudaMemcpyAsync(sc + ql_off, ql, 64, cudaMemcpyHostToDevice, s->stream));
   int* err = (int*)(sc + err_off);
   QS_CUDA(cudaMemsetAsync(err, 0, sizeof(double), s->stream));
+  // the pass that also sums |a|^2: the first one with neither P1 nor view C
+  const int norm_pass = (ENC == 0 && norm_out && np >= 3) ? 1 : -1;
+  if (norm_done) *norm_done = norm_pass >= 0;
   for (int i = 0; i < np; ++i) {
     if (ENC == 0) {
       CUtensorMap map;
@@ -941,8 +958,9 @@ static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz
         return QS_OK;
       };
       const bool vc = i == np - 1;
-      QS_TRY(i == 0 ? (vc ? go(k_expect_tma<true, true>) : go(k_expect_tma<true, false>))
-                    : (vc ? go(k_expect_tma<false, true>) : go(k_expect_tma<false, false>)));
+      if (i == norm_pass) QS_TRY(go(k_expect_tma<false, false, true>));
+      else QS_TRY(i == 0 ? (vc ? go(k_expect_tma<true, true, false>) : go(k_expect_tma<true, false, false>))
+                         : (vc ? go(k_expect_tma<false, true, false>) : go(k_expect_tma<false, false, false>)));
     } else {
       const size_t smem = sizeof(float2) << xv::TB;
       auto go = [&](auto kern) -> qs_status {
@@ -989,6 +1007,7 @@ static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz
         if (i == 0 || k == 2) qz[q] = c[10 + sl];
       }
     }
+  if (norm_pass >= 0) *norm_out = h[res_off[norm_pass] + XNORM_COL];
   return QS_OK;
 }
 
@@ -1014,9 +1033,17 @@ static qs_status expect_small(qs_sim* s, double* qx, double* qy, double* qz) {
 
 qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz) {
   if (s->enc == QS_C128 && s->N >= 12) return expect_impl<double, 4>(s, qx, qy, qz);
-  if (s->enc == QS_C64 && s->N >= 13) return expect_views_impl<0>(s, qx, qy, qz);
-  if (s->enc == QS_ADAPT2 && s->N >= 13) return expect_views_impl<2>(s, qx, qy, qz);
+  if (s->enc == QS_C64 && s->N >= 13) return expect_views_impl<0>(s, qx, qy, qz, nullptr, nullptr);
+  if (s->enc == QS_ADAPT2 && s->N >= 13) return expect_views_impl<2>(s, qx, qy, qz, nullptr, nullptr);
   return expect_small(s, qx, qy, qz);
+}
+
+qs_status launch_expect_norm(qs_sim* s, double* qx, double* qy, double* qz, double* norm) {
+  bool done = false;
+  if (s->enc == QS_C64 && s->N >= 13) QS_TRY(expect_views_impl<0>(s, qx, qy, qz, norm, &done));
+  else QS_TRY(launch_expect(s, qx, qy, qz));
+  if (done) return QS_OK;
+  return (s->enc == QS_ADAPT2) ? a2_norm(s, norm) : launch_norm(s, norm);
 }
 
 template <typename A>

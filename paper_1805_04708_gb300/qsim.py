@@ -90,6 +90,7 @@ _SIGS = {
     "gate_std": (_I, [ctypes.c_char_p, _IP, _I, _D, _I, ctypes.POINTER(qs_gate)]),
     "sim_norm": (_I, [_P, _D]),
     "expect_xyz": (_I, [_P, _D, _D, _D]),
+    "expect_xyz_norm": (_I, [_P, _D, _D, _D, _D]),
     "measure_probs": (_I, [_P, _IP, _I, _D]),
     "measure_probs_static": (_I, [_P, _I, _I, _IP, _I, _D, _P]),
     "sim_copy_out": (_I, [_P, _P, ctypes.c_size_t, _D]),
@@ -368,6 +369,16 @@ class Sim:
         qz = np.empty(self.N)
         _check(_lib.expect_xyz(self._h, qx.ctypes.data_as(_D), qy.ctypes.data_as(_D), qz.ctypes.data_as(_D)))
         return qx, qy, qz
+
+    def expect_xyz_norm(self):
+        """(qx, qy, qz, norm): expect_xyz and norm from one call."""
+        qx = np.empty(self.N)
+        qy = np.empty(self.N)
+        qz = np.empty(self.N)
+        nrm = ctypes.c_double(0.0)
+        _check(_lib.expect_xyz_norm(self._h, qx.ctypes.data_as(_D), qy.ctypes.data_as(_D), qz.ctypes.data_as(_D),
+                                    ctypes.byref(nrm)))
+        return qx, qy, qz, nrm.value
 
     def measure_probs(self, qubits):
         q, nq = _ints(qubits)

@@ -171,7 +171,9 @@ def test_reductions(q, N):
         s.copy_in(a.words(), (a.r0, a.r1))
         nrm = s.norm()
         qx, qy, qz = s.expect_xyz()
+        qx2, qy2, qz2, nrm2 = s.expect_xyz_norm()
         P = s.measure_probs([N - 1, 0, 2])
+    assert nrm2 == nrm and np.array_equal(qx2, qx) and np.array_equal(qy2, qy) and np.array_equal(qz2, qz)
     # the device decodes with FP32 tables: agreement to FP32 precision
     assert abs(nrm - sv.norm(z)) < 1e-6
     rx, ry, rz = sv.expect_xyz(z, N)

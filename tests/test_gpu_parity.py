@@ -182,6 +182,11 @@ def test_reductions(q, enc, N):
         assert np.max(np.abs(qx - rx)) <= tol
         assert np.max(np.abs(qy - ry)) <= tol
         assert np.max(np.abs(qz - rz)) <= tol
+        # both in one call (complex64, N >= 23: one pass also sums |a|^2)
+        qx2, qy2, qz2, nrm2 = s.expect_xyz_norm()
+        assert abs(nrm2 - sv.norm(v)) <= 1e-13
+        for a, b in ((qx2, qx), (qy2, qy), (qz2, qz)):
+            assert np.max(np.abs(a - b)) <= 1e-15
         g = np.random.default_rng(N)
         for nq in sorted({1, min(3, N), min(N, 7)}):
             qs = [int(x) for x in g.choice(N, nq, replace=False)]
