@@ -70,7 +70,7 @@ def product_start_gates(recs):
 
 
 TILE_MODES = {1: "op interpreter k_tile2",
-              2: "per pass structure the fastest of the interpreter and 3 kernels compiled for it (timed once each)",
+              2: "per pass structure the fastest of the interpreter and 3 kernels compiled for it (timed twice each)",
               3: "kernels compiled per pass structure"}
 
 
@@ -251,9 +251,9 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
             qsim.circuit_compile(N, gates, mode=m)
         v["c64_tile_mode%d" % m] = dict(tile_mode(m), kernels=TILE_MODES[m])
     # the same circuit with every gate in the passes (no product start); in
-    # mode 2 the new pass structures take 4 runs to tune
+    # mode 2 the new pass structures take 8 runs to tune
     sim.set_product_start(False)
-    for _ in range(4 if mode == 2 else 0):
+    for _ in range(8 if mode == 2 else 0):
         sim.reset()
         sim.circuit_run(gates, mode=mode)
     v["c64_tile_mode%d_no_product_start" % mode] = dict(tile_mode(mode), kernels=TILE_MODES[mode])
@@ -428,8 +428,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     sim = qsim.Sim(N, "c64", stream=stream)
     # tile-pass kernels: per pass structure the fastest of the interpreter and
-    # the kernels compiled for it (mode 2; compiled here and tried once each
-    # in the warm-up steps, before any timing), else the interpreter
+    # the kernels compiled for it (mode 2; compiled here and tried twice each
+    # in untimed runs, before any timing), else the interpreter
     mode = args.tile_mode
     if mode == 0:
         mode = 2 if qsim.tile_compiler_info()[0] else 1
@@ -437,8 +437,8 @@ def run_gpu(args):
     if mode in (2, 3):
         qsim.circuit_compile(N, gates, mode=mode)
     t_compile = time.perf_counter() - t_compile
-    if mode == 2:   # one untimed run per kernel candidate of every pass structure
-        for _ in range(4):
+    if mode == 2:   # two untimed runs per kernel candidate of every pass structure
+        for _ in range(8):
             sim.reset()
             sim.circuit_run(gates, mode=mode)
 
@@ -541,8 +541,8 @@ def run_profile_case(args):
     state must exceed the 129 MB L2 for DRAM counters to mean something, and
     stay a few GB so that a multi-pass capture ends quickly.
       tile   : the random-gate circuit (N qubits, 200 gates, seed 1) through
-               the tile passes twice (mode 2: after compiling and one run per
-               kernel candidate, four times), then <Qx,Qy,Qz> (complex64)
+               the tile passes twice (mode 2: after compiling and two runs
+               per kernel candidate, four times), then <Qx,Qy,Qz> (complex64)
       fused  : a dense k-qubit gate on qubits 0..k-1, applied three times
                (complex64; the tcgen05 kernel for k >= 3)
       adapt2 : one Haar U(2) on every qubit of the adaptive 2-byte state
@@ -566,9 +566,9 @@ def run_profile_case(args):
         return 0
     with qsim.Sim(N, "c64") as s:
         if args.profile_case == "tile" and args.mode == 2:
-            # compile, then one run per kernel candidate of every pass structure
+            # compile, then two runs per kernel candidate of every pass structure
             qsim.circuit_compile(N, workload_records(N), mode=2)
-            for _ in range(4):
+            for _ in range(8):
                 s.reset()
                 s.circuit_run(workload_records(N), mode=2)
         if args.profile_case == "expect":

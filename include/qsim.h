@@ -204,9 +204,10 @@ qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
  *           qubits and control masks; not its coefficients) the fastest of
  *           the interpreter and three kernels compiled at run time for that
  *           structure (NVRTC, sm_103a; without barriers, and with a CTA
- *           barrier every 2 or every 8 ops).  The first four launches of a
- *           structure try one candidate each, timed with CUDA events on the
- *           handle's stream; later launches use the fastest.  Compiled
+ *           barrier every 2 or every 8 ops).  The first eight launches of
+ *           a structure try each candidate twice, timed with CUDA events on
+ *           the handle's stream; later launches use the candidate with the
+ *           fastest launch.  Compiled
  *           kernels are cached; a new structure pays its compile time unless
  *           circuit_compile ran first; a variant that fails to compile is
  *           never picked.  Compiled kernels (a few hundred KB each) stay

@@ -234,15 +234,28 @@ qs_status tile_jit_launch(qs_sim* s, const TileParams2& P, int sync, unsigned gr
 
 // ---- online choice of the pass kernel (circuit_run mode 2) --------------------
 namespace {
+// Every candidate is timed in kTuneRounds launches (slot n runs candidate
+// n % kTileCands); a candidate's time is the fastest of its launches, so one
+// slow sample (a cold instruction cache, a clock step) does not decide.
+constexpr int kTuneRounds = 2;
+constexpr int kTuneSlots = kTileCands * kTuneRounds;
 struct Tune {
   int next = 0, best = -1;
-  bool launched[kTileCands] = {}, done[kTileCands] = {};
-  float ms[kTileCands] = {};
-  cudaEvent_t ev[kTileCands][2] = {};
+  bool launched[kTuneSlots] = {}, done[kTuneSlots] = {}, failed[kTileCands] = {};
+  float ms[kTuneSlots] = {};
+  cudaEvent_t ev[kTuneSlots][2] = {};
 };
 std::unordered_map<std::string, Tune>& tunes() {
   static std::unordered_map<std::string, Tune> t;
   return t;
+}
+// fastest sample of candidate c so far, or a huge time
+float cand_ms(const Tune& t, int c) {
+  float m = 3.0e38f;
+  if (t.failed[c]) return m;
+  for (int n = c; n < kTuneSlots; n += kTileCands)
+    if (t.done[n] && t.ms[n] < m) m = t.ms[n];
+  return m;
 }
 }  // namespace
 
@@ -254,39 +267,40 @@ qs_status tile_tune_pick(qs_sim* s, const TileParams2& P, int* cand, cudaEvent_t
   Tune& t = tunes()[program_of(P, -1)];
   if (t.best < 0) {
     bool all = true;
-    for (int c = 0; c < kTileCands; ++c) {
-      if (t.launched[c] && !t.done[c] && cudaEventQuery(t.ev[c][1]) == cudaSuccess) {
-        QS_CUDA(cudaEventElapsedTime(&t.ms[c], t.ev[c][0], t.ev[c][1]));
-        t.done[c] = true;
+    for (int n = 0; n < kTuneSlots; ++n) {
+      if (t.launched[n] && !t.done[n] && cudaEventQuery(t.ev[n][1]) == cudaSuccess) {
+        QS_CUDA(cudaEventElapsedTime(&t.ms[n], t.ev[n][0], t.ev[n][1]));
+        t.done[n] = true;
       }
-      all = all && t.done[c];
+      all = all && (t.done[n] || t.failed[n % kTileCands]);
     }
     if (all) {
       t.best = 0;
       for (int c = 1; c < kTileCands; ++c)
-        if (t.ms[c] < t.ms[t.best]) t.best = c;
+        if (cand_ms(t, c) < cand_ms(t, t.best)) t.best = c;
     }
   }
   if (t.best >= 0) {
     *cand = t.best;
     return QS_OK;
   }
-  if (t.next < kTileCands) {
-    const int c = t.next++;
-    if (!t.ev[c][0]) {
-      QS_CUDA(cudaEventCreate(&t.ev[c][0]));
-      QS_CUDA(cudaEventCreate(&t.ev[c][1]));
+  while (t.next < kTuneSlots && t.failed[t.next % kTileCands]) ++t.next;
+  if (t.next < kTuneSlots) {
+    const int n = t.next++;
+    if (!t.ev[n][0]) {
+      QS_CUDA(cudaEventCreate(&t.ev[n][0]));
+      QS_CUDA(cudaEventCreate(&t.ev[n][1]));
     }
-    QS_CUDA(cudaEventRecord(t.ev[c][0], s->stream));
-    t.launched[c] = true;
-    *cand = c;
-    *end_ev = t.ev[c][1];
+    QS_CUDA(cudaEventRecord(t.ev[n][0], s->stream));
+    t.launched[n] = true;
+    *cand = n % kTileCands;
+    *end_ev = t.ev[n][1];
     return QS_OK;
   }
-  // every candidate launched, some still running: the fastest measured so far
+  // every slot launched, some still running: the fastest measured so far
   int best = 0;
   for (int c = 1; c < kTileCands; ++c)
-    if (t.done[c] && (!t.done[best] || t.ms[c] < t.ms[best])) best = c;
+    if (cand_ms(t, c) < cand_ms(t, best)) best = c;
   *cand = best;
   return QS_OK;
 }
@@ -294,6 +308,5 @@ qs_status tile_tune_pick(qs_sim* s, const TileParams2& P, int* cand, cudaEvent_t
 void tile_tune_fail(const TileParams2& P, int cand) {
   std::lock_guard<std::mutex> g(g_mu);
   Tune& t = tunes()[program_of(P, -1)];
-  t.done[cand] = true;
-  t.ms[cand] = 3.0e38f;
+  t.failed[cand] = true;
 }
