@@ -38,10 +38,6 @@ __global__ void __launch_bounds__(TPB, 2) k_tile2(void* __restrict__ s, const __
 // ---------------------------------------------------------------------------------
 // planner
 // ---------------------------------------------------------------------------------
-struct PassPlan {
-  TileParams2 P;
-};
-
 static void fill_u(TOp& o, const double* u) {
   for (int k = 0; k < 8; ++k) { o.ud[k] = u[k]; o.uf[k] = (float)u[k]; }
 }
