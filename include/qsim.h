@@ -214,20 +214,24 @@ qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
  *           loaded until the process ends;
  *   mode 3: the compiled kernel without barriers for every QS_C64 pass.
  * Modes 2 and 3 give QS_EUNSUPPORTED on a QS_C64 state when NVRTC cannot be
- * loaded; QS_C128 states use the interpreter in every tile mode.  Results
- * equal mode 0 up to floating-point rounding order.  gates: host array of n
- * records.  n_passes (may be NULL) receives the number of state sweeps
- * launched.  The paper has no counterpart for modes 1-3. */
+ * loaded; QS_C128 states use the interpreter in every tile mode.  For
+ * QS_C64, a last pass of at most 4 gates joins the previous pass when their
+ * targets fit its tile, and a run from a pending |0..0> starts from the
+ * product state of its leading single-qubit gates (sim_set_product_start).
+ * Results equal mode 0 up to floating-point rounding order.  gates: host
+ * array of n records.  n_passes (may be NULL) receives the number of state
+ * sweeps launched.  The paper has no counterpart for modes 1-3. */
 qs_status circuit_run(qs_sim* sim, const qs_gate* gates, int n, int mode, int* n_passes);
 
 /* Plan the tile passes of a QS_C64 circuit on N qubits (13 <= N <= 63) and
  * compile the kernels of each new pass structure that circuit_run in `mode`
  * may launch (mode 2: its three compiled candidates; mode 3: the one kernel)
  * on up to 16 host threads (host only: no device call; NVRTC must be
- * loadable, else QS_EUNSUPPORTED).  A later circuit_run of the same circuit
- * in that mode then launches without compiling.  n_passes (may be NULL)
- * receives the number of passes planned.  Gate validation as in
- * circuit_run. */
+ * loadable, else QS_EUNSUPPORTED), for runs on a written state and for runs
+ * from a pending |0..0> (the passes after the product start).  A later
+ * circuit_run of the same circuit in that mode then launches without
+ * compiling.  n_passes (may be NULL) receives the number of passes planned
+ * for a written state.  Gate validation as in circuit_run. */
 qs_status circuit_compile(int N, const qs_gate* gates, int n, int mode, int* n_passes);
 
 /* The order in which circuit_run's tile passes take the gates (host only, no
@@ -236,7 +240,8 @@ qs_status circuit_compile(int N, const qs_gate* gates, int n, int mode, int* n_p
  * non-identity gates in run order and pass_start (host, n ints) the position
  * in order where each pass begins; *n_passes the number of passes.  Inside a
  * pass the op rewriting (delayed diagonals, composed neighbours, factor
- * tables) is not shown.  The paper has no counterpart. */
+ * tables) is not shown, and the plan is that of a run on a written state (no
+ * product start).  The paper has no counterpart. */
 qs_status circuit_plan(int N, int enc, const qs_gate* gates, int n, int* order, int* pass_start, int* n_passes);
 
 /* Whether NVRTC could be loaded (available: 1 or 0) and how many pass
