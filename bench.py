@@ -3,9 +3,12 @@
 Workload (one step): a 30-qubit complex64 state (8 GiB, larger than L2, so no
 L2 flush is needed between steps) is reset to |0..0>, an all-Hadamard layer
 and 200 seeded random gates from {H, T, RZ(theta), CNOT, TOFFOLI} on qubits
-0..29 are applied through the native tile-pass planner, then the FP64
-compensated norm and BEGIN MEASUREMENT (<Qx>, <Qy>, <Qz> of every qubit) are
-computed.  Gate-amplitude updates = (logical gates) x 2^N per step.
+0..29 are applied through the native tile-pass planner (the run starts from
+the pending |0..0> of the reset, so its leading single-qubit gates form the
+product start, see sim_set_product_start; every one of the 230 gates is
+counted), then the FP64 compensated norm and BEGIN MEASUREMENT (<Qx>, <Qy>,
+<Qz> of every qubit) are computed in one expect_xyz_norm call.
+Gate-amplitude updates = (logical gates) x 2^N per step.
 
 The same line reports, measured in the same run: the per-gate sweep path, the
 complex128 state (16 GiB), the HBM roofline of the dominant kernel (the
@@ -43,7 +46,7 @@ UNIT = "updates/s"
 # (2 * 2^N * 8 B for complex64)
 # DRAM bytes per tile-pass launch at N = 30, from one ncu capture of the
 # N = 26 random-gate circuit in circuit_run mode 2 (after its kernel choice;
-# interpreter and compiled passes), as the mean over a step's 12 passes of
+# interpreter and compiled passes), as the mean over a step's 8 passes of
 # which the first only writes, scaled by the 16x units
 # (profiles/tile_pass_c64_n26_traffic.md); None when a pass kernel changes
 # after the capture
