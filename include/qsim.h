@@ -244,6 +244,16 @@ qs_status circuit_compile(int N, const qs_gate* gates, int n, int mode, int* n_p
  * product start).  The paper has no counterpart. */
 qs_status circuit_plan(int N, int enc, const qs_gate* gates, int n, int* order, int* pass_start, int* n_passes);
 
+/* The product start of a run of this circuit from a pending |0..0> (host
+ * only, no device call; see sim_set_product_start): *n_prefix receives the
+ * number of gates it takes (the single-qubit gates that come before every
+ * multi-qubit gate on their qubit), factors (host, 4N doubles, or NULL) the
+ * product-state factors f_q(0), f_q(1) of every qubit q as (re, im) pairs,
+ * f_q = U_q |0> with U_q the product of qubit q's gates in order (FP64).
+ * N in 1..63; gate validation as in circuit_run.  The paper has no
+ * counterpart. */
+qs_status circuit_product_start(int N, const qs_gate* gates, int n, int* n_prefix, double* factors);
+
 /* Whether NVRTC could be loaded (available: 1 or 0) and how many pass
  * kernels this process has compiled so far (compiles).  Outputs may be NULL. */
 qs_status tile_compiler_info(int* available, long* compiles);

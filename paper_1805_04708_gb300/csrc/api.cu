@@ -363,6 +363,18 @@ extern "C" qs_status circuit_compile(int N, const qs_gate* gates, int n, int mod
   return compile_tile_passes(N, gates, n, n_passes, mode == 3);
 }
 
+extern "C" qs_status circuit_product_start(int N, const qs_gate* gates, int n, int* n_prefix, double* factors) {
+  CHECK_ARG(N >= 1 && N < 64, "circuit_product_start: N = %d must be in 1..63", N);
+  CHECK_ARG(n >= 0 && (n == 0 || gates != nullptr), "circuit_product_start: bad gate list");
+  CHECK_ARG(n_prefix != nullptr, "circuit_product_start: null n_prefix");
+  qs_sim probe;
+  probe.N = N;
+  probe.enc = QS_C64;
+  for (int i = 0; i < n; ++i) QS_TRY(check_gate(&probe, gates[i]));
+  *n_prefix = product_start_factors(N, gates, n, factors);
+  return QS_OK;
+}
+
 extern "C" qs_status circuit_plan(int N, int enc, const qs_gate* gates, int n, int* order, int* pass_start,
                                   int* n_passes) {
   CHECK_ARG(enc == QS_C128 || enc == QS_C64, "circuit_plan: encoding %d has no tile passes", enc);

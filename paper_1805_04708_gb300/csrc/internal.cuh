@@ -126,6 +126,9 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
 // circuit_run mode 3 launches (all_passes) or every compiled candidate of
 // mode 2.
 qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes, bool all_passes);
+// Product start of a run from |0..0>: number of gates it takes; factors (or
+// null): 4 doubles per qubit, (U_q |0>)(0) and (U_q |0>)(1) as (re, im).
+int product_start_factors(int N, const qs_gate* gates, int n, double* factors);
 // The planner's pass order (host only): order gets the non-identity gate
 // indices in the order the passes take them, pass_start the first position
 // of each pass (both sized n by the caller).

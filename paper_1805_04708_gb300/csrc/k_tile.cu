@@ -472,6 +472,19 @@ static int product_prefix(int N, const qs_gate* g, int n, double (*f)[2][2], std
   return np;
 }
 
+int product_start_factors(int N, const qs_gate* gates, int n, double* factors) {
+  static thread_local double f[64][2][2];
+  std::vector<qs_gate> rest;
+  const int np = product_prefix(N, gates, n, f, &rest);
+  if (factors)
+    for (int q = 0; q < N; ++q)
+      for (int bit = 0; bit < 2; ++bit) {
+        factors[4 * q + 2 * bit] = f[q][bit][0];
+        factors[4 * q + 2 * bit + 1] = f[q][bit][1];
+      }
+  return np;
+}
+
 static uint64_t f2_bits_host(double re, double im) {
   const float fr = (float)re, fi = (float)im;
   uint32_t br, bi;

@@ -86,6 +86,7 @@ _SIGS = {
     "circuit_compile": (_I, [_I, ctypes.POINTER(qs_gate), _I, _I, _IP]),
     "tile_compiler_info": (_I, [_IP, ctypes.POINTER(ctypes.c_long)]),
     "circuit_plan": (_I, [_I, _I, ctypes.POINTER(qs_gate), _I, _IP, _IP, _IP]),
+    "circuit_product_start": (_I, [_I, ctypes.POINTER(qs_gate), _I, _IP, _D]),
     "circuit_run_timed": (_I, [_P, ctypes.POINTER(qs_gate), _I, _I, _IP, ctypes.POINTER(ctypes.c_float), _I]),
     "gate_std": (_I, [ctypes.c_char_p, _IP, _I, _D, _I, ctypes.POINTER(qs_gate)]),
     "sim_norm": (_I, [_P, _D]),
@@ -202,6 +203,19 @@ def circuit_plan(N, gates, enc="c64"):
     used = int(np.count_nonzero(order[:n] >= 0))
     bounds = [int(x) for x in start[:npass.value]] + [used]
     return [[int(x) for x in order[bounds[i]:bounds[i + 1]]] for i in range(npass.value)]
+
+
+def circuit_product_start(N, gates):
+    """The product start of a run from |0..0> (host only): (number of gates it
+    takes, (N, 2) complex array of the factors f_q(0), f_q(1))."""
+    if isinstance(gates, tuple):
+        arr, n = gates
+    else:
+        arr, n = gate_array(gates)
+    f = np.zeros(4 * int(N), dtype=np.float64)
+    npre = ctypes.c_int(0)
+    _check(_lib.circuit_product_start(int(N), arr, n, ctypes.byref(npre), f.ctypes.data_as(_D)))
+    return npre.value, (f[0::2] + 1j * f[1::2]).reshape(int(N), 2)
 
 
 def tile_compiler_info():

@@ -4,7 +4,9 @@ composed per qubit into a product state, and running the remaining gates in
 order on that product state gives the circuit's state.  The library's complex64
 tile runs rely on this (the first pass writes the product state); checked here
 with the oracle alone, against the circuit run gate by gate from |0..0>.  A
-rule that also folds gates after their qubit is entangled must fail."""
+rule that also folds gates after their qubit is entangled must fail.  The
+library's own extraction (circuit_product_start, host only) must take the same
+gates and give the same per-qubit factors."""
 import numpy as np
 import pytest
 
@@ -55,6 +57,23 @@ def test_whole_circuit_product():
     assert rest == []
     ref = circuit.run(sv.zero_state(N), N, recs)
     assert np.max(np.abs(product_state(N, U) - ref)) <= 1e-14
+
+
+@pytest.mark.parametrize("N,kind,seed", [(13, "gate", 1), (16, "mixed", 2), (14, "layered", 3)])
+def test_library_product_start_matches_the_rule(N, kind, seed):
+    # the library's host-side extraction (no GPU work) against the rule above
+    from paper_1805_04708_gb300 import build
+    build.build()
+    from paper_1805_04708_gb300 import qsim
+    recs = {"gate": wl.random_gate_circuit(N, 80, seed=seed),
+            "mixed": wl.random_mixed_circuit(N, 80, seed=seed),
+            "layered": wl.layered_circuit(N, 3, seed=seed)}[kind]
+    U, rest = split(recs)
+    npre, f = qsim.circuit_product_start(N, recs)
+    assert npre == len(recs) - len(rest)
+    for q in range(N):
+        want = U[q][:, 0] if q in U else np.array([1.0, 0.0])
+        assert np.max(np.abs(f[q] - want)) <= 1e-14
 
 
 def test_folding_after_entangling_is_wrong():
