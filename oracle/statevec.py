@@ -156,7 +156,9 @@ def project(v, N, q, bit):
 def csum(x):
     """Compensated sum of a 1-D float64 array: the correctly rounded sum for
     small arrays (math.fsum), else a Neumaier sum down the rows of a 2-D
-    reshaping (vectorised across columns) followed by fsum of the column sums."""
+    reshaping (vectorised across columns) whose running sums and
+    compensation terms are then added exactly (fsum of both, so a large
+    column total that cancels against another keeps its compensation)."""
     x = np.asarray(x, dtype=np.float64).ravel()
     if x.size <= (1 << 20):
         return math.fsum(x.tolist())
@@ -170,7 +172,7 @@ def csum(x):
         big = np.abs(s) >= np.abs(M[r])
         c += np.where(big, (s - t) + M[r], (M[r] - t) + s)
         s = t
-    return math.fsum((s + c).tolist() + x[rows * cols:].tolist())
+    return math.fsum(s.tolist() + c.tolist() + x[rows * cols:].tolist())
 
 
 def csum_rows(M):
