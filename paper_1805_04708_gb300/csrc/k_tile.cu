@@ -636,7 +636,10 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
   if (s->enc == QS_C64 && s->zero_pending && s->product_start &&
       product_prefix(s->N, gates, n, prod, &rest) > 0) {
     k.prod = prod;
-    st = rest.empty() ? run_empty_pass(k) : plan_tile_passes(k, rest.data(), (int)rest.size());
+    // the gates after the prefix may all be identities, which the planner
+    // drops: the product state is still written by one pass
+    st = rest.empty() ? QS_OK : plan_tile_passes(k, rest.data(), (int)rest.size());
+    if (st == QS_OK && k.emitted == 0) st = run_empty_pass(k);
   } else {
     st = plan_tile_passes(k, gates, n);
   }
@@ -654,7 +657,8 @@ qs_status compile_tile_passes(int N, const qs_gate* gates, int n, int* n_passes,
   static thread_local double prod[64][2][2];
   if (product_prefix(N, gates, n, prod, &rest) > 0) {
     PassSink kz = {nullptr, N, QS_C64, all_passes ? 2 : 1, nullptr, 0, &passes, nullptr, nullptr, nullptr};
-    QS_TRY(rest.empty() ? run_empty_pass(kz) : plan_tile_passes(kz, rest.data(), (int)rest.size()));
+    if (!rest.empty()) QS_TRY(plan_tile_passes(kz, rest.data(), (int)rest.size()));
+    if (kz.emitted == 0) QS_TRY(run_empty_pass(kz));
   }
   return tile_jit_compile_all(passes);
 }

@@ -96,3 +96,21 @@ def test_not_from_zero(q):
         s.copy_out()                     # writes the pending |0..0>
         s.circuit_run(recs, mode=1)
         assert maxerr(s.copy_out(), circuit.run(sv.zero_state(N), N, recs)) <= TOL
+
+
+@pytest.mark.parametrize("tail", ["U0", "CMAT_I", "I"])
+def test_prefix_then_only_identities(q, tail):
+    # every gate after the product start is an identity (U(k = 0) is the
+    # controlled phase e^{2 pi i} = 1; an explicit controlled identity; I):
+    # the planner drops them all, and the product state must still be written
+    N = 14
+    ident = {"U0": ("U", (0, 1), (0,)),
+             "CMAT_I": ("CMAT", (3, 5), (1, 0, 0, 0, 0, 0, 1, 0)),
+             "I": ("I", (2,), ())}[tail]
+    recs = [("H", (0,), ()), ("H", (1,), ()), ("U3", (9,), (0.4, 1.1, 2.0)), ident]
+    ref = circuit.run(sv.zero_state(N), N, recs)
+    for mode in modes(q):
+        with q.Sim(N, "c64") as s:
+            npass = s.circuit_run(recs, mode=mode)
+            assert npass == 1
+            assert maxerr(s.copy_out(), ref) <= TOL

@@ -37,6 +37,19 @@ def test_static_matches_measure_probs(q, enc):
                 assert np.max(np.abs(got - ref)) <= 1e-13
 
 
+def test_static_many_complement_indices_per_thread(q):
+    # N = 22: the complement of a small register has more indices than the
+    # fixed 2^18 partial sums, so every partial covers several of them
+    N = 22
+    with q.Sim(N, "c64") as s:
+        s.copy_in(rand_state(N, 12))
+        for qubits in ([7], [21], list(range(16)), list(range(6, 22)), [0, 11, 21]):
+            ref = s.measure_probs(qubits)
+            for _ in range(2):
+                got = q.measure_probs_static(s.device_ptr(), N, "c64", qubits, stream=s.stream_handle)
+                assert np.max(np.abs(got - ref)) <= 1e-13
+
+
 def test_static_rejects_beyond_limit(q):
     N = 18
     with q.Sim(N, "c64") as s:
