@@ -47,9 +47,8 @@ UNIT = "updates/s"
 # DRAM bytes per tile-pass launch at N = 30, from one ncu capture of the
 # N = 26 random-gate circuit in circuit_run mode 2 (after its kernel choice;
 # interpreter and compiled passes), as the mean over a step's 8 passes of
-# which the first only writes, scaled by the 16x units
-# (profiles/tile_pass_c64_n26_traffic.md); None when a pass kernel changes
-# after the capture
+# which the first only writes, scaled by the 16x units; None when a pass
+# kernel changes after the capture
 TILE_TRAFFIC_PER_PASS = 1.5232e10
 
 
@@ -156,53 +155,165 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 # oracle timing (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-CPU_SAMPLE_N = 20
+# The oracle (plain numpy complex128, one thread per process) on the same
+# circuit family at N = 24: its 256 MiB state is larger than the host CPU's
+# caches.  Replicas run in spawned worker processes, one per host core used,
+# each with its own state and the same gate slices, in lock step.
+CPU_SAMPLE_N = 24
+CPU_SLICE = 10          # gates per reference-arm step
+CPU_SAMPLE_GATES = 30   # gates timed per worker for cpu_baseline
 
 
-def oracle_step(N=CPU_SAMPLE_N):
+def _oracle_worker(conn, N, ngates, seed):
     from oracle import circuit, statevec as sv
-    recs = workload_records(N)
-    t0 = time.perf_counter()
-    v = circuit.run(sv.zero_state(N), N, recs)
-    sv.norm(v)
-    sv.expect_xyz(v, N)
-    dt = time.perf_counter() - t0
-    return len(recs) * float(1 << N) / dt, dt
+    recs = workload_records(N, ngates, seed)
+    v = sv.zero_state(N)
+    pos = 0
+    while True:
+        msg = conn.recv()
+        if msg[0] == "stop":
+            return
+        t0 = time.perf_counter()
+        red = 0.0
+        if msg[0] == "gates":
+            for _ in range(msg[1]):
+                circuit.run(v, N, [recs[pos]])
+                pos += 1
+                if pos == len(recs):   # circuit done: its reductions, then a new run
+                    t1 = time.perf_counter()
+                    sv.norm(v)
+                    sv.expect_xyz(v, N)
+                    red += time.perf_counter() - t1
+                    v = sv.zero_state(N)
+                    pos = 0
+        elif msg[0] == "reduce":
+            sv.norm(v)
+            sv.expect_xyz(v, N)
+        conn.send((time.perf_counter() - t0, red))
 
 
-def cpu_baseline(budget_s=20.0):
-    vals, spent = [], 0.0
-    while spent < budget_s:
-        v, dt = oracle_step()
-        vals.append(v)
-        spent += dt
-        if len(vals) >= 3 and spent > budget_s / 2:
-            break
-    return {"value": statistics.median(vals), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "same circuit family at N=%d (%d H + %d gates) + norm + <Qx,Qy,Qz>, "
-                      "numpy complex128, %d runs, median" % (CPU_SAMPLE_N, CPU_SAMPLE_N, N_GATES, len(vals))}
+class OracleReplicas:
+    """`workers` oracle processes (spawned: safe after CUDA calls), each
+    holding its own N-qubit state of the random-gate workload."""
+
+    def __init__(self, workers, N=CPU_SAMPLE_N):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"
+        self.N = N
+        self.conns, self.procs = [], []
+        for _ in range(workers):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, N, N_GATES, SEED), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for k, val in env.items():
+            if val is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = val
+
+    def call(self, *msg):
+        """Send msg to every worker; (wall seconds, per-worker replies)."""
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(msg)
+        rep = [c.recv() for c in self.conns]
+        return time.perf_counter() - t0, rep
+
+    def close(self):
+        for c in self.conns:
+            c.send(("stop",))
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def host_cores():
+    """Host cores available to this process, capped so that every worker's
+    N = 24 state and temporaries (about 1.5 GiB) fit in half the free memory."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable")) * 1024
+        n = min(n, max(1, int(avail / 2 / (1.5 * 2 ** 30))))
+    except (OSError, StopIteration, ValueError):
+        pass
+    return max(1, min(n, 64))
+
+
+def _oracle_sample(workers):
+    """Seconds per gate and per reduction (norm + BEGIN MEASUREMENT) of the
+    oracle with `workers` replicas in lock step (slowest worker)."""
+    rep = OracleReplicas(workers)
+    try:
+        rep.call("gates", 1)                       # first gate: imports, page faults
+        gates_t, r = rep.call("gates", CPU_SAMPLE_GATES)
+        red_t, _ = rep.call("reduce")
+    finally:
+        rep.close()
+    return gates_t / CPU_SAMPLE_GATES, red_t
+
+
+def cpu_baseline():
+    """The oracle on the host cores, as it stands: all cores (one replica per
+    core, the whole-host figure) and one thread.  A bounded sample per
+    worker: 30 gates of the N = 24 workload and one norm + BEGIN
+    MEASUREMENT, scaled to a whole 230-gate step."""
+    ngates = CPU_SAMPLE_N + N_GATES
+    upd = ngates * float(1 << CPU_SAMPLE_N)
+    tg1, tr1 = _oracle_sample(1)
+    one = upd / (ngates * tg1 + tr1)
+    K = host_cores()
+    tgK, trK = _oracle_sample(K) if K > 1 else (tg1, tr1)
+    allc = K * upd / (ngates * tgK + trK)
+    return {"value": allc, "unit": UNIT, "cores": K, "kind": "oracle",
+            "single_thread_value": one,
+            "sample": "oracle (numpy complex128) on the random-gate workload at N=%d (%d H + %d gates, "
+                      "256 MiB state), %d replica processes, one per core, one thread each: %d gates and one "
+                      "norm + <Qx,Qy,Qz> per replica, timed and scaled to the %d-gate step; "
+                      "single_thread_value: the same with one process" % (
+                          CPU_SAMPLE_N, CPU_SAMPLE_N, N_GATES, K, CPU_SAMPLE_GATES, ngates),
+            "config": {"N": CPU_SAMPLE_N, "encoding": "c128 (oracle)"}}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every host core runs a replica of the
+    N = 24 workload; one step = the next 10 gates of the circuit on every
+    replica (after the circuit's last gate a replica computes the norm and
+    BEGIN MEASUREMENT in the same step, then starts again from |0..0>)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        oracle_step()
-    vals, tot = [], 0.0
-    for _ in range(args.steps):
-        v, dt = oracle_step()
-        vals.append(v)
-        tot += dt
-    value = sum(vals) / len(vals)
+    K = host_cores()
+    rep = OracleReplicas(K)
+    try:
+        for _ in range(args.warmup):
+            rep.call("gates", CPU_SLICE)
+        tot = 0.0
+        for _ in range(args.steps):
+            dt, _ = rep.call("gates", CPU_SLICE)
+            tot += dt
+    finally:
+        rep.close()
+    value = K * args.steps * CPU_SLICE * float(1 << CPU_SAMPLE_N) / tot
+    cfg = config_dict(CPU_SAMPLE_N, "c128")
+    cfg["workload"] += " (the oracle's complex128 arithmetic; %d replicas)" % K
+    cfg["l2"] = "host: 256 MiB state per replica, larger than the CPU caches"
+    sample = ("each step: the next %d gates of the N=%d random-gate circuit on each of %d replica processes "
+              "(one per host core); the step that finishes the circuit also computes norm + <Qx,Qy,Qz>"
+              % (CPU_SLICE, CPU_SAMPLE_N, K))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
-        "data": "synthetic", "config": config_dict(N_QUBITS, "c64"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: the circuit family at N=%d (%d H + %d gates) + norm + "
-                                   "<Qx,Qy,Qz> on numpy complex128" % (CPU_SAMPLE_N, CPU_SAMPLE_N, N_GATES)},
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": K, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -3,8 +3,10 @@
 // every gate keeps its own 2x2 matrix, the fusion is in the data movement).
 //
 // A tile is the 2^b amplitudes whose index bits outside the tile bit set are
-// fixed; the set holds the low 6 index bits (512-byte runs) plus the targets
-// of the pass's gates.  Inside a CTA of 256 threads the b local bits are
+// fixed (b = 13 for complex64, 12 for complex128); the set always holds the
+// low LOW_BITS = 4 index bits (16-amplitude runs: 128 B of complex64, 256 B
+// of complex128) plus the targets of the pass's gates, padded with qubits the
+// pass does not touch.  Inside a CTA of 256 threads the b local bits are
 // split three ways:
 //   local bit 0 and RB-1 more local bits  -> register slots (2^RB amplitudes
 //                                             per thread, updated in registers)
@@ -15,8 +17,10 @@
 // a warp bit first swaps that bit into a register slot by one shared-memory
 // transpose.  Diagonal gates run in place whatever their target (the target
 // bit is known for every element), and controls may be any bit (a control
-// outside the tile is a per-tile condition).  Gate order is kept, so the
-// result equals the per-gate sweep up to rounding order.
+// outside the tile is a per-tile condition).  The host planner may take a
+// gate ahead of earlier gates left for later passes only when it commutes
+// with all of them, so the result equals the per-gate sweep up to rounding
+// order.
 //
 // This header holds the device side: it is compiled into the library (the
 // op interpreter, k_tile.cu) and, as source text, into the passes compiled at

@@ -73,6 +73,41 @@ def random_gate_circuit(N, ngates, seed, hadamard_layer=True):
     return recs
 
 
+def block_partition(N, m, seed):
+    """A seeded random partition of the qubits 0..N-1 into blocks of m (the
+    last block takes the remainder), each block's qubits in increasing order."""
+    perm = [int(x) for x in rng(seed).permutation(N)]
+    return [sorted(perm[i:i + m]) for i in range(0, N, m)]
+
+
+def block_gate_circuit(blocks, ngates, seed):
+    """The random-gate family restricted to blocks of qubits: an
+    all-Hadamard layer, then `ngates` gates drawn uniformly from {H, T,
+    RZ(theta), U3 (random angles), CNOT, TOFFOLI}, each on distinct qubits of
+    one uniformly chosen block (blocks too small for a gate redraw).  Every
+    gate stays inside its block, so the final state is a tensor product of
+    one state per block."""
+    g = rng(seed)
+    N = sum(len(b) for b in blocks)
+    recs = [("H", (q,), ()) for q in range(N)]
+    kinds = ("H", "T", "RZ", "U3", "CNOT", "TOFFOLI")
+    while len(recs) < N + ngates:
+        k = kinds[int(g.integers(len(kinds)))]
+        b = blocks[int(g.integers(len(blocks)))]
+        need = {"CNOT": 2, "TOFFOLI": 3}.get(k, 1)
+        if len(b) < need:
+            continue
+        q = tuple(int(b[i]) for i in g.choice(len(b), need, replace=False))
+        if k == "RZ":
+            p = (float(g.uniform(0.0, 2.0 * math.pi)),)
+        elif k == "U3":
+            p = tuple(float(x) for x in g.uniform(0.0, 2.0 * math.pi, 3))
+        else:
+            p = ()
+        recs.append((k, q, p))
+    return recs
+
+
 def random_mixed_circuit(N, ngates, seed, max_controls=2):
     """Gates of every kind the instruction set has (random angles, random
     Haar matrices, 0..max_controls controls) on random distinct qubits; used
