@@ -20,6 +20,12 @@ adapt2    : the 2-byte adaptive polar encoding of Sec. 4.1, step by step.
 shor      : the classical side of Shor's algorithm (Sec. 5.4) and the
             closed-form x-register distribution after SHORBOX + QFT.
 circuit   : runs a gate list (mnemonic records) through statevec / adapt2.
+measure   : M, CLEAR, SET, GENERATE EVENTS and the DEPOLARIZING CHANNEL of
+            Appendix A, with the SplitMix64 counter-based generator for
+            seeded draws.
+program   : parses and runs a program in the instruction language of
+            Appendix A (the front-end), on the complex128 oracle or the
+            adaptive encoding's emulation.
 
 Parity pins: every function here is pinned in ``tests/test_oracle_*.py``
 against brute force, closed forms or the paper's printed tables.  Functions

@@ -220,6 +220,39 @@ def error_correction_example(errors=(0,)):
     return recs, stage1
 
 
+def program_text(N, records, bit_assignment=None, noise=None):
+    """Program text in the instruction language of Appendix A for gate
+    records; further instruction lines may be appended by the caller.
+    noise: (p_x, p_y, p_z, seed) for a DEPOLARIZING CHANNEL line."""
+    lines = ["QUBITS %d" % N]
+    if bit_assignment is not None:
+        lines.append("BIT ASSIGNMENT " + " ".join(str(int(x)) for x in bit_assignment))
+    if noise is not None:
+        lines.append("DEPOLARIZING CHANNEL P_X = %r, P_Y = %r, P_Z = %r, SEED = %d" % tuple(noise))
+    for name, qs, ps in records:
+        lines.append(" ".join([name] + [str(int(q)) for q in qs] + [repr(p) for p in ps]))
+    return "\n".join(lines) + "\n"
+
+
+def error_correction_program(errors=(0,), events=8192, seed=-1):
+    """The Appendix B error-correction example as a program: preparation and
+    encoding, BEGIN MEASUREMENT, bit-flip errors on `errors`, syndrome
+    extraction with projective measurements M 3 and M 4 before the
+    correction, re-preparation of qubit 3 (H, CLEAR) and qubit 4 (H, SET),
+    BEGIN MEASUREMENT, and GENERATE EVENTS."""
+    recs, stage1 = error_correction_example(errors)
+    nerr = len(errors)
+    syndrome = recs[stage1 + nerr: stage1 + nerr + 4]
+    correct = recs[stage1 + nerr + 4:]
+    body = program_text(5, recs[:stage1]).splitlines()
+    body.append("BEGIN MEASUREMENT")
+    body += program_text(5, recs[stage1: stage1 + nerr] + syndrome).splitlines()[1:]
+    body += ["M 3", "M 4"]
+    body += program_text(5, correct).splitlines()[1:]
+    body += ["H 3", "CLEAR 3", "H 4", "SET 4", "BEGIN MEASUREMENT", "GENERATE EVENTS %d %d" % (events, seed)]
+    return "\n".join(body) + "\n"
+
+
 def serving_stream(n, rate, seed, nmin=12, nmax=28, dmin=10, dmax=100):
     """Requests for the serving loop: Poisson arrivals at `rate` per second,
     N ~ U{nmin..nmax}, depth ~ U{dmin..dmax}, each with its own circuit seed."""
