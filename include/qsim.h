@@ -321,6 +321,112 @@ qs_status measure_probs(qs_sim* sim, const int* qubits, int nq, double* out);
 qs_status measure_probs_static(const void* state, int N, qs_encoding enc, const int* qubits, int nq,
                                double* out, void* cuda_stream);
 
+/* ---- stochastic instructions (Appendix A: M, CLEAR, SET, GENERATE EVENTS,
+ *      DEPOLARIZING CHANNEL) ----------------------------------------------- */
+/* Every random number is an argument: a uniform draw in [0, 1).  A caller
+ * with a seed instead gets the draws from qs_uniforms (SplitMix64 of Steele,
+ * Lea and Flood, OOPSLA 2014, evaluated at (seed, counter)), the generator
+ * that generate_events_seeded and depolarize_circuit use. */
+
+/* out[k] = uniform draw number first + k of `seed`: the top 53 bits of
+ * SplitMix64's output for counter first + k, times 2^-53 (host only). */
+qs_status qs_uniforms(uint64_t seed, uint64_t first, int64_t n, double* out);
+
+/* M q (Appendix A): p0, p1 = probabilities of outcomes 0, 1 of qubit q (FP64
+ * sums of |a|^2 over the two halves, Sec. 2); outcome = 0 if u (p0 + p1) <
+ * p0, else 1 (inverse CDF over the outcomes); then the state is projected
+ * onto the outcome and renormalised (multiplied by 1/sqrt(p_outcome)).
+ * outcome (host int) and probs (host, 2 doubles: p0, p1) may be NULL.  u must
+ * lie in [0, 1).  QS_EZEROPROJ for a state of zero norm.  QS_ADAPT2 states
+ * re-encode with a re-tuned (r0, r1) (an arithmetic operation, Sec. 4.1).
+ * Synchronises the stream (the outcome comes back to the host). */
+qs_status measure_qubit(qs_sim* sim, int q, double u, int* outcome, double* probs);
+
+/* CLEAR q (bit = 0) / SET q (bit = 1) (Appendix A): the projection
+ * |bit><bit| on qubit q, renormalised.  prob (host, may be NULL) receives the
+ * probability of `bit` before the projection.  If that probability is
+ * exactly zero the projection would give a zero state: QS_EZEROPROJ, the
+ * state unchanged (the failure the appendix prescribes).  Synchronises. */
+qs_status project_qubit(qs_sim* sim, int q, int bit, double* prob);
+
+/* GENERATE EVENTS (Appendix A): n basis states sampled from the
+ * probabilities |a_i|^2 of the current state.  Event k is the smallest index
+ * i with C_i > u[k] C_last, C_i = sum_{j <= i} |a_j|^2 (inverse CDF in index
+ * order, FP64 sums in a fixed order); where rounding moves a target across a
+ * boundary the event is the neighbouring index, and an index whose
+ * amplitude is exactly zero is never drawn.  u: host, n draws in [0, 1);
+ * events: host, n uint64 indices (bit q = qubit q).  1 <= n <= 2^31.  The
+ * state is left unchanged (the appendix lets the simulator stop here).
+ * Device scratch: about 2^(N-10) * 16 bytes plus 16 bytes per event.
+ * Synchronises. */
+qs_status generate_events(qs_sim* sim, const double* u, int64_t n, uint64_t* events);
+/* The same with u[k] = qs_uniforms(seed, k) drawn on the device. */
+qs_status generate_events_seeded(qs_sim* sim, uint64_t seed, int64_t n, uint64_t* events);
+
+/* DEPOLARIZING CHANNEL P_X = px, P_Y = py, P_Z = pz, SEED = seed (Appendix
+ * A), as a circuit transformation on the host: after gate g of `gates` and
+ * for every qubit q, the draw r = qs_uniforms(seed, (first_gate + g) N + q)
+ * inserts X (r < px), Y (px <= r < px + py), Z (px + py <= r < px + py + pz)
+ * or nothing.  (first_gate numbers gates across successive calls.)  out:
+ * host, room for cap records; *n_out receives the number of records the
+ * noisy circuit has.  With out == NULL only *n_out is computed (QS_OK); with
+ * a cap too small, QS_EINVAL.  Requires 0 <= px, py, pz and px + py + pz <= 1. */
+qs_status depolarize_circuit(int N, const qs_gate* gates, int n, double px, double py, double pz,
+                             uint64_t seed, int64_t first_gate, qs_gate* out, int cap, int* n_out);
+
+/* ---- the instruction language of Appendix A (front-end) --------------------- */
+/* A program is text, one instruction per line, '!' starting a comment, case
+ * ignored: QUBITS N (first), BIT ASSIGNMENT p_0 .. p_{N-1}, the gate
+ * mnemonics with their qubits then their numbers (the operand order of
+ * gate_std: "U1 n lambda", "U c t k", "TOFFOLI c1 c2 t", ...; also RZ),
+ * BEGIN MEASUREMENT, M n, CLEAR n, SET n, SHORBOX n_x G y, DEPOLARIZING
+ * CHANNEL P_X = p, P_Y = p, P_Z = p, SEED = k (any order, any subset),
+ * GENERATE EVENTS events [seed], EXIT.  The paper has no C interface; these
+ * calls run its instruction list on a state handle. */
+typedef struct qs_program qs_program;
+
+/* Parse program text (host).  Errors: QS_EINVAL with the line number and the
+ * reason in qs_last_error_string (unknown mnemonic, qubit out of range or
+ * repeated, wrong operand count, QUBITS missing or not first, BIT ASSIGNMENT
+ * not a permutation, probabilities out of range). */
+qs_status program_parse(const char* text, qs_program** out);
+qs_status program_destroy(qs_program* prog);
+/* Number of qubits and of instructions after QUBITS. */
+qs_status program_info(const qs_program* prog, int* N, int* n_instr);
+
+/* Run the program on `sim` (same N; reset to |0..0> first).  Consecutive
+ * gates run as one circuit_run in `mode` (QS_ADAPT2 states always per gate).
+ * BIT ASSIGNMENT p: logical qubit k is stored in index bit p[k] from then on
+ * (before any gate nothing moves; later the stored qubits are moved with
+ * permute_qubits); every result is per logical qubit, events in logical bit
+ * order.  Draws: M number m uses qs_uniforms(run_seed, m); GENERATE EVENTS n
+ * s uses seed s, or run_seed + 1 when s <= 0 (the paper's "system value");
+ * the depolarizing channel draws qs_uniforms(seed, g N + q) for gate
+ * operation g of the program and logical qubit q, seed = SEED, or run_seed +
+ * 2 when SEED <= 0.  GENERATE EVENTS and EXIT end the run (EXIT records one
+ * BEGIN MEASUREMENT).  A CLEAR / SET with a zero projection returns
+ * QS_EZEROPROJ.  Results stay in `prog` until the next run. */
+qs_status program_run(qs_program* prog, qs_sim* sim, uint64_t run_seed, int mode);
+/* Counts of the last run's results: BEGIN MEASUREMENT tables, M outcomes,
+ * CLEAR / SET projections, events.  Outputs may be NULL. */
+qs_status program_results(const qs_program* prog, int* n_measurements, int* n_m, int* n_proj, int64_t* n_events);
+/* Table k (0-based) of BEGIN MEASUREMENT: qx, qy, qz (host, N doubles each). */
+qs_status program_expectations(const qs_program* prog, int k, double* qx, double* qy, double* qz);
+/* Per M in order: logical qubit, outcome, (p0, p1) before the projection;
+ * per CLEAR / SET: the probability of the kept outcome.  Host arrays sized
+ * by program_results; any may be NULL. */
+qs_status program_outcomes(const qs_program* prog, int* qubits, int* outcomes, double* probs, double* proj_probs);
+/* The events of GENERATE EVENTS (host, n_events uint64). */
+qs_status program_events(const qs_program* prog, uint64_t* events);
+
+/* Move the stored qubits: the content of index bit k goes to index bit
+ * perm[k] (perm: host, a permutation of 0..N-1), i.e. amplitude i moves to
+ * the index whose bit perm[k] is bit k of i.  In place, as transpositions of
+ * bits (three CNOTs each, through the tile passes; bit-exact moves).  The
+ * BIT ASSIGNMENT of Appendix A renumbers qubits this way (Sec. 3.2 motivates
+ * it by the communication it saves). */
+qs_status permute_qubits(qs_sim* sim, const int* perm);
+
 /* ---- batched small states ------------------------------------------------- */
 /* Many independent N-qubit states advanced through their own gate lists in
  * one launch (each gate is the pair update of Eq. (NUM2) / Eq. (AQS0); the

@@ -70,7 +70,10 @@ def parse(text):
             elif up.startswith("BEGIN MEASUREMENT"):
                 prog.append(("BEGIN MEASUREMENT", ()))
             elif up.startswith("GENERATE EVENTS"):
-                prog.append(("GENERATE EVENTS", (int(toks[2]), int(toks[3]) if len(toks) > 3 else 0)))
+                nev = int(toks[2])
+                if not 1 <= nev <= 2 ** 31:
+                    raise ValueError("events out of range")
+                prog.append(("GENERATE EVENTS", (nev, int(toks[3]) if len(toks) > 3 else 0)))
             elif up.startswith("DEPOLARIZING CHANNEL"):
                 kv = dict(P_X=0.0, P_Y=0.0, P_Z=0.0, SEED=0)
                 for key, val in re.findall(r"(P_X|P_Y|P_Z|SEED)\s*=\s*([-+0-9.eE]+)", up):
@@ -85,7 +88,10 @@ def parse(text):
                     raise ValueError("qubit out of range")
                 prog.append((toks[0], (q,)))
             elif toks[0] == "SHORBOX":
-                prog.append(("SHORBOX", (int(toks[1]), int(toks[2]), int(toks[3]))))
+                nx, G, y = int(toks[1]), int(toks[2]), int(toks[3])
+                if not (1 <= nx < N and G >= 2 and 1 <= y < G and G <= 2 ** (N - nx)):
+                    raise ValueError("SHORBOX arguments out of range")
+                prog.append(("SHORBOX", (nx, G, y)))
             elif toks[0] == "EXIT":
                 prog.append(("EXIT", ()))
             elif toks[0] in GATES_1Q or toks[0] in NQUBIT:

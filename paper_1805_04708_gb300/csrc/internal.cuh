@@ -147,6 +147,9 @@ struct A2Dev {
 qs_status a2_set_range(qs_sim* s, double r0, double r1);
 qs_status a2_get_range(qs_sim* s, double* r0, double* r1);
 qs_status a2_apply_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]);
+// The same update always through the arithmetic path (decode, apply, re-tune
+// (r0, r1), encode), for non-unitary updates such as a scaled projection.
+qs_status a2_apply_arith(qs_sim* s, const int* controls, int nc, int target, const double u[8]);
 qs_status a2_norm(qs_sim* s, double* out);
 qs_status a2_shorbox(qs_sim* s, int nx, uint64_t G, uint64_t y);
 qs_status a2_reset(qs_sim* s);

@@ -391,6 +391,18 @@ qs_status a2_apply_u2(qs_sim* s, const int* controls, int nc, int target, const 
   return a2_arith(s, g, op);
 }
 
+qs_status a2_apply_arith(qs_sim* s, const int* controls, int nc, int target, const double u[8]) {
+  Geo g;
+  g.N = s->N;
+  g.t = target;
+  g.cmask = 0;
+  for (int i = 0; i < nc; ++i) g.cmask |= 1ull << controls[i];
+  auto fcx = [&](int k) { Cx<float> c; c.x = (float)u[2 * k]; c.y = (float)u[2 * k + 1]; return c; };
+  OpDense<float> op;
+  op.u00 = fcx(0); op.u01 = fcx(1); op.u10 = fcx(2); op.u11 = fcx(3);
+  return a2_arith(s, g, op);
+}
+
 qs_status a2_norm(qs_sim* s, double* out) {
   const A2Dev* d = (const A2Dev*)s->a2dev;
   if (s->N < 4) {

@@ -94,6 +94,22 @@ _SIGS = {
     "expect_xyz_norm": (_I, [_P, _D, _D, _D, _D]),
     "measure_probs": (_I, [_P, _IP, _I, _D]),
     "measure_probs_static": (_I, [_P, _I, _I, _IP, _I, _D, _P]),
+    "qs_uniforms": (_I, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _D]),
+    "measure_qubit": (_I, [_P, _I, ctypes.c_double, _IP, _D]),
+    "project_qubit": (_I, [_P, _I, _I, _D]),
+    "generate_events": (_I, [_P, _D, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]),
+    "generate_events_seeded": (_I, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]),
+    "program_parse": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "program_destroy": (_I, [_P]),
+    "program_info": (_I, [_P, _IP, _IP]),
+    "program_run": (_I, [_P, _P, ctypes.c_uint64, _I]),
+    "program_results": (_I, [_P, _IP, _IP, _IP, ctypes.POINTER(ctypes.c_int64)]),
+    "program_expectations": (_I, [_P, _I, _D, _D, _D]),
+    "program_outcomes": (_I, [_P, _IP, _IP, _D, _D]),
+    "program_events": (_I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "permute_qubits": (_I, [_P, _IP]),
+    "depolarize_circuit": (_I, [_I, ctypes.POINTER(qs_gate), _I, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(qs_gate), _I, _IP]),
     "sim_copy_out": (_I, [_P, _P, ctypes.c_size_t, _D]),
     "sim_copy_in": (_I, [_P, _P, ctypes.c_size_t, _D]),
     "sim_sync": (_I, [_P]),
@@ -224,6 +240,79 @@ def tile_compiler_info():
     c = ctypes.c_long(0)
     _check(_lib.tile_compiler_info(ctypes.byref(a), ctypes.byref(c)))
     return bool(a.value), int(c.value)
+
+
+def uniforms(seed, first, n):
+    """Draws first .. first + n - 1 of the library's counter-based generator."""
+    out = np.empty(int(n))
+    _check(_lib.qs_uniforms(int(seed) & (2 ** 64 - 1), int(first), int(n), out.ctypes.data_as(_D)))
+    return out
+
+
+def depolarize_circuit(N, gates, px, py, pz, seed, first_gate=0):
+    """The circuit with the depolarizing channel's Pauli gates inserted (a
+    ctypes qs_gate array and its length)."""
+    if isinstance(gates, tuple):
+        arr, n = gates
+    else:
+        arr, n = gate_array(gates)
+    need = ctypes.c_int(0)
+    _check(_lib.depolarize_circuit(int(N), arr, n, float(px), float(py), float(pz), int(seed) & (2 ** 64 - 1),
+                                   int(first_gate), None, 0, ctypes.byref(need)))
+    out = (qs_gate * max(1, need.value))()
+    _check(_lib.depolarize_circuit(int(N), arr, n, float(px), float(py), float(pz), int(seed) & (2 ** 64 - 1),
+                                   int(first_gate), out, need.value, ctypes.byref(need)))
+    return out, need.value
+
+
+class Program:
+    """A parsed program in the instruction language of Appendix A."""
+
+    def __init__(self, text):
+        h = _P()
+        _check(_lib.program_parse(text.encode(), ctypes.byref(h)))
+        self._h = h
+        n, ni = ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib.program_info(h, ctypes.byref(n), ctypes.byref(ni)))
+        self.N, self.n_instr = n.value, ni.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.program_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, sim, run_seed=1, mode=1):
+        """Run on a Sim of N qubits; returns dict(measurements=[(qx, qy,
+        qz), ...], m=[(qubit, outcome, p0, p1), ...], proj=[p, ...],
+        events=array)."""
+        _check(_lib.program_run(self._h, sim._h, int(run_seed) & (2 ** 64 - 1), int(mode)))
+        nm, nmm, npj = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        nev = ctypes.c_int64(0)
+        _check(_lib.program_results(self._h, ctypes.byref(nm), ctypes.byref(nmm), ctypes.byref(npj),
+                                    ctypes.byref(nev)))
+        meas = []
+        for k in range(nm.value):
+            x, y, z = np.empty(self.N), np.empty(self.N), np.empty(self.N)
+            _check(_lib.program_expectations(self._h, k, x.ctypes.data_as(_D), y.ctypes.data_as(_D),
+                                             z.ctypes.data_as(_D)))
+            meas.append((x, y, z))
+        qs = np.zeros(max(1, nmm.value), dtype=np.int32)
+        os_ = np.zeros(max(1, nmm.value), dtype=np.int32)
+        pr = np.zeros(2 * max(1, nmm.value))
+        pj = np.zeros(max(1, npj.value))
+        _check(_lib.program_outcomes(self._h, qs.ctypes.data_as(_IP), os_.ctypes.data_as(_IP),
+                                     pr.ctypes.data_as(_D), pj.ctypes.data_as(_D)))
+        ev = np.zeros(max(1, nev.value), dtype=np.uint64)
+        _check(_lib.program_events(self._h, ev.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        m = [(int(qs[i]), int(os_[i]), float(pr[2 * i]), float(pr[2 * i + 1])) for i in range(nmm.value)]
+        return dict(measurements=meas, m=m, proj=[float(x) for x in pj[:npj.value]],
+                    events=ev[:nev.value].astype(np.int64))
 
 
 # ---------------------------------------------------------------------------
@@ -399,6 +488,38 @@ class Sim:
         out = np.empty(1 << nq)
         _check(_lib.measure_probs(self._h, q, nq, out.ctypes.data_as(_D)))
         return out
+
+    def permute_qubits(self, perm):
+        """The content of index bit k moves to index bit perm[k]."""
+        p, n = _ints(perm)
+        _check(_lib.permute_qubits(self._h, p))
+
+    # -- stochastic instructions --
+    def measure(self, q, u):
+        """M q with the draw u: (outcome, p0, p1); the state is projected."""
+        o = ctypes.c_int(0)
+        pr = np.zeros(2)
+        _check(_lib.measure_qubit(self._h, int(q), float(u), ctypes.byref(o), pr.ctypes.data_as(_D)))
+        return o.value, float(pr[0]), float(pr[1])
+
+    def project(self, q, bit):
+        """CLEAR q (bit 0) / SET q (bit 1); returns the probability of `bit`."""
+        p = ctypes.c_double(0.0)
+        _check(_lib.project_qubit(self._h, int(q), int(bit), ctypes.byref(p)))
+        return p.value
+
+    def generate_events(self, u=None, n=None, seed=None):
+        """Basis-state events from the draws u, or n events from `seed`."""
+        if u is not None:
+            u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+            out = np.empty(u.size, dtype=np.uint64)
+            _check(_lib.generate_events(self._h, u.ctypes.data_as(_D), u.size,
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        else:
+            out = np.empty(int(n), dtype=np.uint64)
+            _check(_lib.generate_events_seeded(self._h, int(seed) & (2 ** 64 - 1), int(n),
+                                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out.astype(np.int64)
 
     # -- raw access --
     def copy_out(self):
