@@ -23,6 +23,9 @@ circuit   : runs a gate list (mnemonic records) through statevec / adapt2.
 measure   : M, CLEAR, SET, GENERATE EVENTS and the DEPOLARIZING CHANNEL of
             Appendix A, with the SplitMix64 counter-based generator for
             seeded draws.
+aux       : the auxiliary-variable method of Sec. 4.2 (discrete
+            Hubbard-Stratonovich rewrite of controlled phases, amplitudes as a
+            sum over 2^P sign configurations of single-qubit products).
 program   : parses and runs a program in the instruction language of
             Appendix A (the front-end), on the complex128 oracle or the
             adaptive encoding's emulation.

@@ -108,6 +108,34 @@ def block_gate_circuit(blocks, ngates, seed):
     return recs
 
 
+def aux_circuit(N, n_entangling, n_single, seed, toffoli=0):
+    """A circuit for the auxiliary-variable method (Sec. 4.2): an
+    all-Hadamard layer, then n_single single-qubit gates (H, T, RZ, U3) and
+    n_entangling CNOT or controlled-phase U(k) gates (plus `toffoli` TOFFOLI
+    gates) in random order on random distinct qubits."""
+    g = rng(seed)
+    kinds = ["1"] * n_single + ["2"] * n_entangling + ["3"] * toffoli
+    order = g.permutation(len(kinds))
+    recs = [("H", (q,), ()) for q in range(N)]
+    for i in order:
+        k = kinds[int(i)]
+        if k == "1":
+            name = ("H", "T", "RZ", "U3")[int(g.integers(4))]
+            q = (int(g.integers(N)),)
+            p = {"RZ": (float(g.uniform(0, 2 * math.pi)),),
+                 "U3": tuple(float(x) for x in g.uniform(0, 2 * math.pi, 3))}.get(name, ())
+            recs.append((name, q, p))
+        elif k == "2":
+            q = tuple(int(x) for x in g.choice(N, 2, replace=False))
+            if g.integers(2):
+                recs.append(("CNOT", q, ()))
+            else:
+                recs.append(("U", q, (int(g.integers(-6, 7)),)))
+        else:
+            recs.append(("TOFFOLI", tuple(int(x) for x in g.choice(N, 3, replace=False)), ()))
+    return recs
+
+
 def random_mixed_circuit(N, ngates, seed, max_controls=2):
     """Gates of every kind the instruction set has (random angles, random
     Haar matrices, 0..max_controls controls) on random distinct qubits; used
