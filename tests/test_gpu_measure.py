@@ -103,8 +103,12 @@ def test_zero_projection_fails_and_keeps_state(q, enc):
             assert np.array_equal(before[0], after[0])
         else:
             assert np.array_equal(before, after)
-        # SET on the same qubit keeps everything (probability 1)
-        assert abs(s.project(2, 1) - 1.0) <= 1e-12
+        # SET on the same qubit keeps everything: its probability is the
+        # stored state's whole norm (complex64 rounds 1/sqrt(2))
+        if enc == "adapt2":
+            assert abs(s.project(2, 1) - 1.0) <= 1e-6
+        else:
+            assert abs(s.project(2, 1) - sv.norm(np.asarray(before, np.complex128))) <= 1e-12
 
 
 def test_measure_adapt2_against_emulation(q):
