@@ -398,8 +398,10 @@ qs_status program_info(const qs_program* prog, int* N, int* n_instr);
  * gates run as one circuit_run in `mode` (QS_ADAPT2 states always per gate).
  * BIT ASSIGNMENT p: logical qubit k is stored in index bit p[k] from then on
  * (before any gate nothing moves; later the stored qubits are moved with
- * permute_qubits); every result is per logical qubit, events in logical bit
- * order.  Draws: M number m uses qs_uniforms(run_seed, m); GENERATE EVENTS n
+ * permute_qubits); every result is per logical qubit.  GENERATE EVENTS
+ * first moves the qubits back to their own bits (the run ends there), so the
+ * inverse CDF walks the logical index order and the events do not depend on
+ * the renumbering.  Draws: M number m uses qs_uniforms(run_seed, m); GENERATE EVENTS n
  * s uses seed s, or run_seed + 1 when s <= 0 (the paper's "system value");
  * the depolarizing channel draws qs_uniforms(seed, g N + q) for gate
  * operation g of the program and logical qubit q, seed = SEED, or run_seed +
@@ -426,6 +428,29 @@ qs_status program_events(const qs_program* prog, uint64_t* events);
  * BIT ASSIGNMENT of Appendix A renumbers qubits this way (Sec. 3.2 motivates
  * it by the communication it saves). */
 qs_status permute_qubits(qs_sim* sim, const int* perm);
+
+/* ---- auxiliary-variable amplitudes (Sec. 4.2) ------------------------------- */
+/* M amplitudes <z_m| C |0..0> of the circuit C without the 2^N state: every
+ * CNOT, controlled phase U(k), controlled diagonal unitary and TOFFOLI is
+ * rewritten into single-qubit gates and controlled phase shifts U_ct(a)
+ * (Eq. (appa4); CNOT = H U(pi) H, TOFFOLI by the standard H / T / CNOT
+ * decomposition), each U_ct(a) into a sum over one auxiliary variable
+ * s = +-1 of single-qubit factors diag(e^{i th}, e^{-i th}) on c and t with
+ * th = x s - a/4, cos 2x = e^{ia/2} (Eqs. (appa5), (appa6)); the amplitude is
+ * 2^-P times the sum over all 2^P configurations of the product over qubits
+ * of (W_j(s)|0>)(bit j of z) (Eq. (appa7)).  One device thread per
+ * configuration, FP64, fixed-order sums (deterministic).  gates: host, n
+ * records (single-qubit gates, or nc = 1 with an X or a diagonal unitary, or
+ * nc = 2 with an X; others give QS_EUNSUPPORTED); basis: host, M indices
+ * < 2^N (bit q = qubit q), 1 <= M <= 4096; out: host, 2M doubles (re, im);
+ * *P_out (may be NULL) the number of auxiliary variables, at most 40 (more
+ * gives QS_EINVAL).  N <= 63: the state is never formed.  Work grows as 2^P;
+ * device memory: a few KB, allocated and freed on cuda_stream (NULL =
+ * default stream).  Synchronises the stream. */
+qs_status aux_amplitudes(int N, const qs_gate* gates, int n, const uint64_t* basis, int M, double* out,
+                         int* P_out, void* cuda_stream);
+/* The number P of auxiliary variables of a circuit (host only). */
+qs_status aux_count(int N, const qs_gate* gates, int n, int* P);
 
 /* ---- batched small states ------------------------------------------------- */
 /* Many independent N-qubit states advanced through their own gate lists in

@@ -7,9 +7,11 @@
 // Consecutive gate instructions are collected and run as one circuit_run, so
 // the tile planner sees whole gate runs.  BIT ASSIGNMENT renumbers where the
 // qubits are stored: logical qubit k lives in index bit perm[k] from then on;
-// every result is reported per logical qubit (events in logical bit order).
-// Before any gate the renumbering moves nothing (the state is |0..0>);
-// later it permutes the stored amplitudes (permute_qubits).
+// every result is reported per logical qubit.  Before any gate the
+// renumbering moves nothing (the state is |0..0>); later it permutes the
+// stored amplitudes (permute_qubits).  GENERATE EVENTS first moves the qubits
+// back to their own bits, so that the inverse CDF walks the logical index
+// order and the events do not depend on the renumbering.
 //
 // Seeds (the paper takes the system's value for a seed <= 0; here the run's
 // seed stands in, so runs repeat): M number m draws qs_uniforms(run_seed, m);
@@ -390,16 +392,20 @@ extern "C" qs_status program_run(qs_program* p, qs_sim* s, uint64_t run_seed, in
         break;
       }
       case PI_EVENTS: {
-        const uint64_t es = in.seed > 0 ? (uint64_t)in.seed : run_seed + 1;
-        std::vector<uint64_t> ev(in.nev);
-        QS_TRY(generate_events_seeded(s, es, in.nev, ev.data()));
-        for (auto& e : ev) {   // index bits -> logical qubit order
-          uint64_t l = 0;
-          for (int k = 0; k < N; ++k) l |= ((e >> map[k]) & 1ull) << k;
-          e = l;
+        // the inverse CDF walks the index order: sample with the qubits back
+        // in their logical bits, so the events do not depend on the
+        // renumbering (the run ends here)
+        bool ident = true;
+        for (int k = 0; k < N; ++k) ident &= (map[k] == k);
+        if (!ident) {
+          int sigma[64];
+          for (int k = 0; k < N; ++k) sigma[map[k]] = k;
+          QS_TRY(permute_qubits(s, sigma));
+          for (int k = 0; k < N; ++k) map[k] = k;
         }
-        p->events = std::move(ev);
-        return QS_OK;
+        const uint64_t es = in.seed > 0 ? (uint64_t)in.seed : run_seed + 1;
+        p->events.assign(in.nev, 0);
+        return generate_events_seeded(s, es, in.nev, p->events.data());
       }
       case PI_EXIT:
         return measure_all();

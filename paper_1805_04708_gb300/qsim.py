@@ -108,6 +108,8 @@ _SIGS = {
     "program_outcomes": (_I, [_P, _IP, _IP, _D, _D]),
     "program_events": (_I, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "permute_qubits": (_I, [_P, _IP]),
+    "aux_amplitudes": (_I, [_I, ctypes.POINTER(qs_gate), _I, ctypes.POINTER(ctypes.c_uint64), _I, _D, _IP, _P]),
+    "aux_count": (_I, [_I, ctypes.POINTER(qs_gate), _I, _IP]),
     "depolarize_circuit": (_I, [_I, ctypes.POINTER(qs_gate), _I, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(qs_gate), _I, _IP]),
     "sim_copy_out": (_I, [_P, _P, ctypes.c_size_t, _D]),
@@ -263,6 +265,28 @@ def depolarize_circuit(N, gates, px, py, pz, seed, first_gate=0):
     _check(_lib.depolarize_circuit(int(N), arr, n, float(px), float(py), float(pz), int(seed) & (2 ** 64 - 1),
                                    int(first_gate), out, need.value, ctypes.byref(need)))
     return out, need.value
+
+
+def aux_amplitudes(N, gates, basis, stream=0):
+    """Amplitudes <z|C|0..0> for the basis indices z by the auxiliary-variable
+    method (Sec. 4.2): (complex array, number of auxiliary variables)."""
+    if isinstance(gates, tuple):
+        arr, n = gates
+    else:
+        arr, n = gate_array(gates)
+    b = np.ascontiguousarray(np.asarray(basis, dtype=np.uint64))
+    out = np.empty(2 * b.size)
+    P = ctypes.c_int(0)
+    _check(_lib.aux_amplitudes(int(N), arr, n, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), b.size,
+                               out.ctypes.data_as(_D), ctypes.byref(P), _P(int(stream))))
+    return out[0::2] + 1j * out[1::2], P.value
+
+
+def aux_count(N, gates):
+    arr, n = gates if isinstance(gates, tuple) else gate_array(gates)
+    P = ctypes.c_int(0)
+    _check(_lib.aux_count(int(N), arr, n, ctypes.byref(P)))
+    return P.value
 
 
 class Program:
