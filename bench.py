@@ -663,9 +663,12 @@ def run_profile_case(args):
                (the range and encode passes of each arithmetic gate)
       expect : BEGIN MEASUREMENT (<Qx,Qy,Qz> of every qubit) twice on the
                state after the random-gate circuit (complex64)
-      ops    : four single-pass circuits of one op class each (complex64):
-               an empty pass, 20 H on register-slot qubits, 21 H on lane
-               qubits, 20 U3 on register-slot qubits"""
+      ops    : single-pass circuits of one op class each (complex64, in
+               circuit_run --mode): an empty pass, 20 H on register-slot
+               qubits, 21 H on lane qubits, 20 U3 on register-slot qubits,
+               20 CNOT between register slots, 20 CNOT and 20 TOFFOLI with
+               controls outside the tile, 21 CNOT on lane targets with a
+               register-slot control, 20 RZ on register slots"""
     import numpy as np
     import torch
     from paper_1805_04708_gb300 import qsim
@@ -693,11 +696,19 @@ def run_profile_case(args):
             top = N - 1
             slots = [0, top - 6, top - 5, top - 4, top - 3]      # register slots
             lanes = [1, 2, 3]                                    # lane qubits
-            for recs in ([("T", (top,), ())],
-                         [("H", (q,), ()) for q in slots] * 4,
-                         [("H", (q,), ()) for q in lanes] * 7,
-                         [("U3", (q,), (0.3, 0.5, 0.7)) for q in slots] * 4):
-                s.circuit_run(recs, mode=1)
+            outer = 10                                           # a control outside the tile
+            pairs = [(slots[i], slots[(i + 1) % 5]) for i in range(5)]
+            cases = [[("T", (top,), ())],
+                     [("H", (q,), ()) for q in slots] * 4,
+                     [("H", (q,), ()) for q in lanes] * 7,
+                     [("U3", (q,), (0.3, 0.5, 0.7)) for q in slots] * 4,
+                     [("CNOT", c_t, ()) for c_t in pairs] * 4,
+                     [("CNOT", (outer, q), ()) for q in slots] * 4,
+                     [("TOFFOLI", (outer, outer + 1, q), ()) for q in slots] * 4,
+                     [("CNOT", (slots[1], q), ()) for q in lanes] * 7,
+                     [("RZ", (q,), (0.1 * (k + 1),)) for k, q in enumerate(slots * 4)]]
+            for recs in cases:
+                s.circuit_run(recs, mode=args.mode)
         elif args.profile_case == "tile":
             recs = wl.random_gate_circuit(N, N_GATES, SEED)
             for _ in range(4 if args.mode == 2 else 2):
