@@ -49,7 +49,7 @@ UNIT = "updates/s"
 # interpreter and compiled passes), as the mean over a step's 8 passes of
 # which the first only writes, scaled by the 16x units; None when a pass
 # kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = 1.5232e10
+TILE_TRAFFIC_PER_PASS = None
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
@@ -446,20 +446,102 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
         torch.cuda.empty_cache()
     v["shor_n30_modmul_iqft"] = sh
 
-    # depth-1 layers of the Haar + CNOT-matching family at the full sizes:
-    # adaptive 2-byte N = 36 (128 GiB) and complex128 N = 33 (128 GiB)
-    for enc, NN in (("adapt2", 36), ("c128", 33)):
-        s = qsim.Sim(NN, enc, stream=stream)
-        layer = wl.layered_circuit(NN, 1, seed=3)
-        mode = 0 if enc == "adapt2" else 1
-        ms, _ = _timed(torch, stream, lambda: s.circuit_run(layer, mode=mode))
-        msn, nrm = _timed(torch, stream, lambda: s.norm())
-        v["%s_n%d_layer" % (enc, NN)] = {"gates": len(layer), "ms_per_layer": ms,
-                                         "value": len(layer) * float(1 << NN) / (ms / 1e3),
-                                         "norm_after_layer": nrm, "norm_ms": msn}
-        s.close()
-        del s
+    # the layered Haar + CNOT-matching family at depth 10: the adaptive 2-byte
+    # encoding against the FP64 state of the same circuit at N = 16..28,
+    # layer by layer (norm, fidelity |<e|a>|^2 / (<a|a><e|e>), relative
+    # distance ||a - e|| / ||e||, both states on the device, sim_overlap)
+    curve = {}
+    for NN in (16, 20, 24, 28):
+        e = qsim.Sim(NN, "c128", stream=stream)
+        a = qsim.Sim(NN, "adapt2", stream=stream)
+        recs = wl.layered_circuit(NN, 10, seed=3)
+        per = NN + NN // 2
+        rows, t_a = [], 0.0
+        for L in range(10):
+            layer = recs[L * per:(L + 1) * per]
+            e.circuit_run(layer, mode=1)
+            ms, _ = _timed(torch, stream, lambda: a.circuit_run(layer, mode=0))
+            t_a += ms
+            ov, d2 = e.overlap(a)
+            ne, na = e.norm(), a.norm()
+            rows.append({"layer": L + 1, "norm_adapt2": na, "fidelity": abs(ov) ** 2 / (ne * na),
+                         "rel_distance": math.sqrt(d2 / ne)})
+        curve["N%d" % NN] = {"layers": rows, "adapt2_ms_per_layer": t_a / 10}
+        e.close()
+        a.close()
+        del e, a
         torch.cuda.empty_cache()
+    v["adapt2_vs_fp64_depth10"] = curve
+
+    # full sizes: adaptive 2-byte N = 36 (128 GiB) at depth 10 with the FP64
+    # compensated norm after every layer (stops after 60 s of layers), and
+    # one layer of complex128 N = 33 (128 GiB)
+    s = qsim.Sim(36, "adapt2", stream=stream)
+    recs = wl.layered_circuit(36, 10, seed=3)
+    per = 36 + 18
+    layers, t_tot = [], 0.0
+    for L in range(10):
+        layer = recs[L * per:(L + 1) * per]
+        ms, _ = _timed(torch, stream, lambda: s.circuit_run(layer, mode=0))
+        msn, nrm = _timed(torch, stream, lambda: s.norm())
+        t_tot += ms
+        layers.append({"layer": L + 1, "ms": ms, "norm": nrm, "norm_ms": msn})
+        if t_tot > 60e3:
+            break
+    v["adapt2_n36_depth10"] = {"gates_per_layer": per, "layers_run": len(layers), "layers": layers,
+                               "value": len(layers) * per * float(1 << 36) / (t_tot / 1e3)}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    s = qsim.Sim(33, "c128", stream=stream)
+    layer = wl.layered_circuit(33, 1, seed=3)
+    ms, _ = _timed(torch, stream, lambda: s.circuit_run(layer, mode=1))
+    msn, nrm = _timed(torch, stream, lambda: s.norm())
+    v["c128_n33_layer"] = {"gates": len(layer), "ms_per_layer": ms,
+                           "value": len(layer) * float(1 << 33) / (ms / 1e3), "norm_after_layer": nrm,
+                           "norm_ms": msn}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # the stochastic instructions on the N = 30 complex64 state of the bench
+    # circuit (M, CLEAR, GENERATE EVENTS) and the same circuit with the
+    # depolarizing channel (p_x = p_y = p_z = 0.001: Pauli gates inserted)
+    s = qsim.Sim(N, "c64", stream=stream)
+    s.circuit_run(gates, mode=1)
+    st = {}
+    ms, out = _timed(torch, stream, lambda: s.measure(7, 0.3))
+    st["M_ms"] = ms
+    try:
+        ms, _ = _timed(torch, stream, lambda: s.project(3, 0))
+        st["CLEAR_ms"] = ms
+    except qsim.QSError as ex:   # a zero projection cannot happen here; record it if it does
+        st["CLEAR_error"] = str(ex)
+    for nev in (8192, 1 << 20):
+        s.generate_events(n=nev, seed=1)
+        ms, _ = _timed(torch, stream, lambda: s.generate_events(n=nev, seed=1))
+        st["events_%d_ms" % nev] = ms
+    noisy = qsim.depolarize_circuit(N, gates, 0.001, 0.001, 0.001, 5)
+    s.reset()
+    s.circuit_run(noisy, mode=1)
+    ms, _ = _timed(torch, stream, lambda: (s.reset(), s.circuit_run(noisy, mode=1)))
+    st["depolarized_circuit"] = {"records": noisy[1], "ms": ms}
+    v["stochastic_ops_c64_n30"] = st
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # auxiliary-variable amplitudes (Sec. 4.2) beyond any state vector: N = 48,
+    # 24 entangling gates (P = 24 auxiliary variables), 64 amplitudes
+    recs = wl.aux_circuit(48, 24, 96, 4)
+    basis = [int(x) for x in np.random.default_rng(4).integers(0, 1 << 48, 64, dtype=np.int64)]
+    qsim.aux_amplitudes(48, recs, basis[:8])
+    t0 = time.perf_counter()
+    amps, P = qsim.aux_amplitudes(48, recs, basis)
+    dt = time.perf_counter() - t0
+    v["aux_amplitudes_n48"] = {"N": 48, "P": P, "amplitudes": len(basis), "s": dt,
+                               "amplitude_terms_per_s": float(1 << P) * len(basis) / dt,
+                               "max_abs_amplitude": float(np.max(np.abs(amps)))}
 
     # serving: a bounded sample of the request stream (Poisson 200/s,
     # N ~ U{12..28}, depth ~ U{10..100}), continuous batching vs the plain
@@ -698,7 +780,8 @@ def run_profile_case(args):
             lanes = [1, 2, 3]                                    # lane qubits
             outer = 10                                           # a control outside the tile
             pairs = [(slots[i], slots[(i + 1) % 5]) for i in range(5)]
-            cases = [[("T", (top,), ())],
+            cases = [[("T", (top,), ())],      # from the pending |0..0>: writes only
+                     [("T", (top,), ())],
                      [("H", (q,), ()) for q in slots] * 4,
                      [("H", (q,), ()) for q in lanes] * 7,
                      [("U3", (q,), (0.3, 0.5, 0.7)) for q in slots] * 4,

@@ -297,6 +297,16 @@ qs_status expect_xyz(qs_sim* sim, double* qx, double* qy, double* qz);
  * |a|^2).  norm: host, one double.  Errors as expect_xyz. */
 qs_status expect_xyz_norm(qs_sim* sim, double* qx, double* qy, double* qz, double* norm);
 
+/* Overlap of two states of the same N on the same device, any encodings:
+ * ov (host, 2 doubles) = <a|b> = sum_i conj(a_i) b_i as (re, im), and
+ * *dist2 = ||a - b||^2 = sum_i |a_i - b_i|^2, both FP64 in a fixed order
+ * (adaptive words decoded with their own (r0, r1)).  The fidelity of the two
+ * states is |<a|b>|^2 / (<a|a> <b|b>).  The paper compares its two
+ * simulators, double precision and the 2-byte encoding, on the same circuits
+ * (Sec. 4.1, Tables 4-6); this is the device form of that comparison.  Runs on
+ * a's stream after b's pending work; synchronises a's stream. */
+qs_status sim_overlap(qs_sim* a, qs_sim* b, double* ov, double* dist2);
+
 /* Marginal distribution of the nq qubits `qubits` (Sec. 2: the probability
  * of outcome 0/1 for a single qubit, generalised to a register):
  * out[k] = sum over basis states whose qubit qubits[m] equals bit m of k of

@@ -31,7 +31,19 @@ constexpr unsigned int INF_BITS = 0x7f800000u;
 struct EncP {
   float r0, r1, scale;
 };
-__device__ __forceinline__ float a2_mag(Cx<float> z) { return sqrtf(fmaf(z.x, z.x, z.y * z.y)); }
+// |z| below about 1e-18 has a square that is denormal or zero in FP32; such
+// magnitudes are taken from the scaled components instead, so that the range
+// and the codes of tiny amplitudes follow |z| as the FP64 definition does
+constexpr float TINY2 = 1e-36f;
+__device__ __forceinline__ float tiny_mag(Cx<float> z) {
+  const float ax = fabsf(z.x), ay = fabsf(z.y);
+  const float s = fmaxf(ax, ay), t = fminf(ax, ay) / s;
+  return s * sqrtf(fmaf(t, t, 1.f));
+}
+__device__ __forceinline__ float a2_mag(Cx<float> z) {
+  const float m2 = fmaf(z.x, z.x, z.y * z.y);
+  return (m2 < TINY2 && (z.x != 0.f || z.y != 0.f)) ? tiny_mag(z) : sqrtf(m2);
+}
 
 __device__ __forceinline__ unsigned int a2_enc(Cx<float> z, const EncP& e) {
   if (z.x == 0.f && z.y == 0.f) return 0x0080u;
@@ -69,16 +81,22 @@ __device__ EncP enc_params(const A2Dev* d) {
 // block_minmax), and for a float m2, sqrtf(m2) < 1 exactly when m2 < 1 (the
 // float below 1 has its root below the midpoint of 1 - 2^-24 and 1) and
 // sqrtf(m2) > 0 exactly when m2 > 0.
-__device__ __forceinline__ void track(Cx<float> z, float& mn2, float& mx2) {
+// A nonzero amplitude whose square is below TINY2 goes to mn as its
+// magnitude (tiny_mag); mn2 / mx2 track the others' squares.
+__device__ __forceinline__ void track(Cx<float> z, float& mn2, float& mx2, float& mnt) {
   const float m2 = fmaf(z.x, z.x, z.y * z.y);
-  if (m2 > 0.f && m2 < 1.f) { mn2 = fminf(mn2, m2); mx2 = fmaxf(mx2, m2); }
+  if (m2 >= TINY2 && m2 < 1.f) { mn2 = fminf(mn2, m2); mx2 = fmaxf(mx2, m2); }
+  else if (m2 < TINY2 && (z.x != 0.f || z.y != 0.f)) mnt = fminf(mnt, tiny_mag(z));
 }
 
-// mn2 / mx2: the thread's min / max of squared magnitudes (INF / 0 if none)
-__device__ void block_minmax(float mn2, float mx2, A2Dev* d) {
+// mn2 / mx2: the thread's min / max of squared magnitudes (INF / 0 if none);
+// mnt: its smallest tiny magnitude (INF if none)
+__device__ void block_minmax(float mn2, float mx2, float mnt, A2Dev* d) {
   __shared__ float smn[32], smx[32];
   float mn = (mn2 < __uint_as_float(INF_BITS)) ? sqrtf(mn2) : mn2;
+  mn = fminf(mn, mnt);
   float mx = sqrtf(mx2);
+  if (mx2 == 0.f && mnt < __uint_as_float(INF_BITS)) mx = mnt;   // only tiny values seen
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -117,7 +135,7 @@ __global__ void __launch_bounds__(TPB) k_a2_arith(uint16_t* __restrict__ st, Geo
   build_luts(L, d->r0, d->r1);
   EncP e;
   if (PASS == 1) e = enc_params(d);
-  float mn = __uint_as_float(INF_BITS), mx = 0.f;
+  float mn = __uint_as_float(INF_BITS), mx = 0.f, mnt = __uint_as_float(INF_BITS);
   uint4* s4 = (uint4*)st;
   const uint64_t nchunks = 1ull << (g.N - 3);
   const uint64_t nunits = (g.t >= 3) ? (nchunks >> 1) : nchunks;
@@ -130,7 +148,7 @@ __global__ void __launch_bounds__(TPB) k_a2_arith(uint16_t* __restrict__ st, Geo
         Cx<float> a = a2_dec(L, wget(w0, k)), b = a2_dec(L, wget(w1, k));
         const uint64_t i0 = c0 * 8 + k;
         if ((i0 & g.cmask) == g.cmask) op.pair(a, b);
-        if (PASS == 0) { track(a, mn, mx); track(b, mn, mx); }
+        if (PASS == 0) { track(a, mn, mx, mnt); track(b, mn, mx, mnt); }
         else { wset(w0, k, a2_enc(a, e)); wset(w1, k, a2_enc(b, e)); }
       }
       if (PASS == 1) { s4[c0] = w0; s4[c1] = w1; }
@@ -143,13 +161,13 @@ __global__ void __launch_bounds__(TPB) k_a2_arith(uint16_t* __restrict__ st, Geo
         Cx<float> a = a2_dec(L, wget(w, k)), b = a2_dec(L, wget(w, k | m));
         const uint64_t i0 = u * 8 + k;
         if ((i0 & g.cmask) == g.cmask) op.pair(a, b);
-        if (PASS == 0) { track(a, mn, mx); track(b, mn, mx); }
+        if (PASS == 0) { track(a, mn, mx, mnt); track(b, mn, mx, mnt); }
         else { wset(w, k, a2_enc(a, e)); wset(w, k | m, a2_enc(b, e)); }
       }
       if (PASS == 1) s4[u] = w;
     }
   }
-  if (PASS == 0) block_minmax(mn, mx, d);
+  if (PASS == 0) block_minmax(mn, mx, mnt, d);
 }
 
 // Small states (N < 4): one thread per pair, plain word accesses.
@@ -159,16 +177,16 @@ __global__ void k_a2_arith_small(uint16_t* __restrict__ st, Geo g, Op op, A2Dev*
   build_luts(L, d->r0, d->r1);
   EncP e;
   if (PASS == 1) e = enc_params(d);
-  float mn = __uint_as_float(INF_BITS), mx = 0.f;
+  float mn = __uint_as_float(INF_BITS), mx = 0.f, mnt = __uint_as_float(INF_BITS);
   const uint64_t npairs = 1ull << (g.N - 1);
   for (uint64_t p = threadIdx.x; p < npairs; p += blockDim.x) {
     const uint64_t i0 = ins0(p, g.t), i1 = i0 | (1ull << g.t);
     Cx<float> a = a2_dec(L, st[i0]), b = a2_dec(L, st[i1]);
     if ((i0 & g.cmask) == g.cmask) op.pair(a, b);
-    if (PASS == 0) { track(a, mn, mx); track(b, mn, mx); }
+    if (PASS == 0) { track(a, mn, mx, mnt); track(b, mn, mx, mnt); }
     else { st[i0] = (uint16_t)a2_enc(a, e); st[i1] = (uint16_t)a2_enc(b, e); }
   }
-  if (PASS == 0) block_minmax(mn, mx, d);
+  if (PASS == 0) block_minmax(mn, mx, mnt, d);
 }
 
 __global__ void k_a2_begin(A2Dev* d) { d->mn = INF_BITS; d->mx = 0u; }

@@ -260,10 +260,10 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
       o.a = (uint8_t)reg_slot(p);
     }
     // complex64: real matrices take the packed FP32x2 path, except pure swaps
-    // on lane qubits (those only exchange values)
+    // (X, CNOT, TOFFOLI: those only exchange values)
     const bool real = (g.u[1] == 0.0 && g.u[3] == 0.0 && g.u[5] == 0.0 && g.u[7] == 0.0);
     const bool pure_swap = (gc.kind == GK_ANTI && gc.c0 == 0 && gc.c1 == 0);
-    if (real_kinds && real && !diag && (o.type == T_REG || (o.type == T_LANE && !pure_swap))) o.kind = GK_REAL;
+    if (real_kinds && real && !diag && !pure_swap && (o.type == T_REG || o.type == T_LANE)) o.kind = GK_REAL;
     P->ops[nops++] = o;
   }
   // diagonal ops commute: inside each run of them, put the register-slot ones
@@ -697,20 +697,20 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
   const uint64_t gmax = (uint64_t)s->num_sms * 2;   // two persistent CTAs per SM
   const unsigned grid = (unsigned)(ntiles < gmax ? ntiles : gmax);
   if (s->enc == QS_C128) {
-    const size_t smem = ((size_t)16 << P.b) + 16 * sizeof(uint64_t);
+    const size_t smem = ((size_t)16 << P.b) + tile_smem_header(4);
     QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
   } else if (cand > 0) {
-    const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
+    const size_t smem = ((size_t)8 << P.b) + tile_smem_header(5);
     QS_TRY(tile_jit_launch(s, P, kTileCandSync[cand], grid, smem));
   } else {
     int feat = 0;
     for (int i = 0; i < P.nops; ++i) {
       const TOp& o = P.ops[i];
-      if (o.type == T_LANE && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) feat |= FEAT_SWAP;
+      if ((o.type == T_LANE || o.type == T_REG) && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) feat |= FEAT_SWAP;
       if ((o.type == T_REG || o.type == T_LANE) && (o.kind == GK_REAL || o.kind == GK_BFLY)) feat |= FEAT_HAD;
     }
-    const size_t smem = ((size_t)8 << P.b) + 32 * sizeof(uint64_t);
+    const size_t smem = ((size_t)8 << P.b) + tile_smem_header(5);
     auto go = [&](auto kern) -> qs_status {
       QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       kern<<<grid, TPB, smem, s->stream>>>(s->state, P);

@@ -122,6 +122,15 @@ __device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b)
   return g;
 }
 
+// exchange of the two values of a pair (X-type gates: unit coefficients)
+template <typename R> struct OpSwapC {
+  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
+    const Cx<R> t = a0;
+    a0 = a1;
+    a1 = t;
+  }
+};
+
 // --- register-slot pair op, slot S fixed at compile time -----------------------------
 template <typename R, int RB, int S, typename F>
 __device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) {
@@ -327,9 +336,16 @@ __device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t bas
   }
 }
 
+// Bytes of the shared-memory header of a tile pass (before the 16-byte
+// aligned tile buffer): 2^RB uint64 global offsets and 2^(RB-1) uint32 local
+// indices.
+__host__ __device__ constexpr unsigned tile_smem_header(int RB) {
+  return (unsigned)(((8u << RB) + (4u << (RB - 1)) + 15u) & ~15u);
+}
+
 // FEAT: which specialised complex64 paths the pass needs (bit 0: swaps, bit 1:
 // Hadamard-shaped); passes without them run a smaller kernel.
-constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_HAD: real-matrix path (packed FP32x2)
+constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_SWAP: X-type exchanges; FEAT_HAD: real-matrix path (packed FP32x2)
 
 // 16-byte global -> shared copies that bypass registers (LDGSTS), so the next
 // tile's loads are in flight while the current tile is computed and stored.
@@ -351,12 +367,15 @@ __device__ __forceinline__ Cx<float> cmul_f(Cx<float> a, Cx<float> b) {
 
 // Each thread stages exactly the 16-byte chunks it will read back, so the
 // stage buffer needs no barrier: the thread's own wait_group orders it.
+// lreg[jj]: the local index of register 2 jj under the load map with the
+// thread part 0 (tile-invariant, formed once per CTA), so a register's local
+// index is tl | lreg[jj].
 template <typename R, int RB>
 __device__ __forceinline__ void stage_tile(const void* s, Cx<R>* st, uint64_t base, const uint64_t* roff, uint64_t woff,
-                                           const TMap& m, uint32_t tl) {
+                                           const uint32_t* lreg, uint32_t tl) {
 #pragma unroll
   for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
+    const uint32_t l = tl | lreg[jj];
     const uint64_t g = base + woff + roff[jj];
     if constexpr (sizeof(R) == 4) {
       cp_async16(((float4*)st) + (l >> 1), ((const float4*)s) + (g >> 1));
@@ -368,10 +387,10 @@ __device__ __forceinline__ void stage_tile(const void* s, Cx<R>* st, uint64_t ba
   cp_async_commit();
 }
 template <typename R, int RB>
-__device__ __forceinline__ void unstage_tile(const Cx<R>* st, Cx<R>* v, const TMap& m, uint32_t tl) {
+__device__ __forceinline__ void unstage_tile(const Cx<R>* st, Cx<R>* v, const uint32_t* lreg, uint32_t tl) {
 #pragma unroll
   for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
-    const uint32_t l = lidx<RB>(m, 2 * jj, tl);
+    const uint32_t l = tl | lreg[jj];
     if constexpr (sizeof(R) == 4) {
       const float4 x = ((const float4*)st)[l >> 1];
       v[2 * jj] = cx<float>(x.x, x.y);
@@ -392,15 +411,18 @@ template <typename R, int RB, int FEAT, class Prog>
 __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams2& P) {
   extern __shared__ unsigned char smraw[];
   constexpr int NR = 1 << RB;
-  // global offsets of the register part (pairs jj: slots 1..RB-1) at load / store
+  // global offsets of the register part (pairs jj: slots 1..RB-1) at load /
+  // store, and the local indices of the register part at load
   uint64_t* roff_in = (uint64_t*)smraw;
   uint64_t* roff_out = roff_in + NR / 2;
+  uint32_t* lreg_in = (uint32_t*)(roff_out + NR / 2);
   // transpose buffer, 2^b elements; between the last transpose of a tile and
   // the start of the next it stages the next tile
-  Cx<R>* xb = (Cx<R>*)(smraw + NR * sizeof(uint64_t));
+  Cx<R>* xb = (Cx<R>*)(smraw + tile_smem_header(RB));
   Cx<R>* stg = xb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < NR / 2) {
+    lreg_in[threadIdx.x] = lidx<RB>(P.init, 2 * threadIdx.x, 0);
     roff_in[threadIdx.x] = goff(lidx<RB>(P.init, 2 * threadIdx.x, 0), P.gpos, P.b);
     roff_out[threadIdx.x] = goff(lidx<RB>(P.fin, 2 * threadIdx.x, 0), P.gpos, P.b);
   }
@@ -423,12 +445,19 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
       fthr = cmul_f(fthr, pf_at(P, q, (tl_in >> k) & 1));
     }
   }
-  if (load && blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, deposit_t(blockIdx.x, P.out_mask), roff_in, woff_in, P.init, tl_in);
+  // tile tau starts at base = deposit(tau) (its bits spread over the bits
+  // outside the tile); the next tile of this CTA, tau + gridDim.x, starts at
+  // deposit(tau) + deposit(gridDim.x) added in the deposited domain: the
+  // gaps set to ones carry across them
+  const uint64_t dstep = deposit_t(gridDim.x, P.out_mask);
+  const uint64_t gaps = ~P.out_mask;
+  uint64_t base = deposit_t(blockIdx.x, P.out_mask);
+  if (load && blockIdx.x < ntiles) stage_tile<R, RB>(s, stg, base, roff_in, woff_in, lreg_in, tl_in);
   for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
-    const uint64_t base = deposit_t(tau, P.out_mask);
+    const uint64_t base_nxt = ((base | gaps) + dstep) & P.out_mask;
     if (load) {
       cp_async_wait_all();
-      unstage_tile<R, RB>(stg, v, P.init, tl_in);
+      unstage_tile<R, RB>(stg, v, lreg_in, tl_in);
     } else if (sizeof(R) == 4 && P.from_product) {
       // product state: thread factor x the factors of the qubits outside the
       // tile x the register table
@@ -450,7 +479,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
     }
     const uint64_t nxt = tau + gridDim.x;
     if (load && P.last_xpose < 0 && nxt < ntiles)
-      stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
+      stage_tile<R, RB>(s, stg, base_nxt, roff_in, woff_in, lreg_in, tl_in);
     TMap cur = P.init;
     uint32_t tl = thread_part(cur, lane, warp);
     Cx<R> fac = cx<R>((R)1, (R)0);
@@ -493,7 +522,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
         }
         __syncthreads();
         if (load && i == P.last_xpose && nxt < ntiles)
-          stage_tile<R, RB>(s, stg, deposit_t(nxt, P.out_mask), roff_in, woff_in, P.init, tl_in);
+          stage_tile<R, RB>(s, stg, base_nxt, roff_in, woff_in, lreg_in, tl_in);
         continue;
       }
       const bool gok = (base & st.gmask) == st.gmask;       // outer controls
@@ -522,7 +551,11 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
             // of X, Y, CNOT, TOFFOLI)
             // (a register-slot swap as renames makes the register allocation
             // spill at 128 registers; swaps on register slots stay dense)
-            if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
+            if ((FEAT & FEAT_SWAP) && st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0) {
+              // X-type (X, CNOT, TOFFOLI): the pair only exchanges values
+              OpSwapC<R> f;
+              reg_op<R, RB>(v, st.a, st.smask, f);
+            } else if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
               OpBflyF f;
               reg_op<R, RB>(v, st.a, st.smask, f);
             } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY)) {
@@ -604,6 +637,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
       }
     }
     store_tile<R, RB>(s, v, base, roff_out, woff_out, lane);
+    base = base_nxt;
   }
 }
 

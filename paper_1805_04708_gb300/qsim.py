@@ -94,6 +94,7 @@ _SIGS = {
     "expect_xyz_norm": (_I, [_P, _D, _D, _D, _D]),
     "measure_probs": (_I, [_P, _IP, _I, _D]),
     "measure_probs_static": (_I, [_P, _I, _I, _IP, _I, _D, _P]),
+    "sim_overlap": (_I, [_P, _P, _D, _D]),
     "qs_uniforms": (_I, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _D]),
     "measure_qubit": (_I, [_P, _I, ctypes.c_double, _IP, _D]),
     "project_qubit": (_I, [_P, _I, _I, _D]),
@@ -506,6 +507,13 @@ class Sim:
         _check(_lib.expect_xyz_norm(self._h, qx.ctypes.data_as(_D), qy.ctypes.data_as(_D), qz.ctypes.data_as(_D),
                                     ctypes.byref(nrm)))
         return qx, qy, qz, nrm.value
+
+    def overlap(self, other):
+        """(<self|other>, ||self - other||^2) in FP64 (any encodings)."""
+        ov = np.zeros(2)
+        d2 = ctypes.c_double(0.0)
+        _check(_lib.sim_overlap(self._h, other._h, ov.ctypes.data_as(_D), ctypes.byref(d2)))
+        return complex(ov[0], ov[1]), d2.value
 
     def measure_probs(self, qubits):
         q, nq = _ints(qubits)

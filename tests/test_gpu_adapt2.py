@@ -211,3 +211,72 @@ def test_shor_accuracy(q):
     qz = shor.qz_from_distribution(P / P.sum(), X)
     qz_ref = shor.qz_from_distribution(shor.closed_form_distribution(X, r), X)
     assert np.max(np.abs(qz - qz_ref)) < 0.01
+
+
+@pytest.mark.parametrize("N,depth", [(18, 2), (20, 1)])
+def test_layered_circuit_stepwise_tie_policy(q, N, depth):
+    # every gate of a layered circuit at N = 18 / 20, each checked against the
+    # oracle applied to the device's own input codes (decode, exact gate,
+    # re-tune, encode): code moves exact, arithmetic gates within the tie
+    # policy, so no gate of the whole circuit drifts from the oracle
+    recs = wl.layered_circuit(N, depth, seed=N + 5)
+    flips = total = 0
+    with q.Sim(N, "adapt2") as s:
+        for rec in recs:
+            w, r = s.copy_out()
+            before = a2.AState(N, *a2.unpack(w), r[0], r[1])
+            ref = circuit.run_adapt2(before.copy(), [rec])
+            s.circuit_run([rec], mode=0)
+            w2, r2 = s.copy_out()
+            b0, b1 = a2.unpack(w2)
+            if rec[0] == "CNOT":
+                assert np.array_equal(b0, ref.b0) and np.array_equal(b1, ref.b1)
+                assert r2 == r
+            else:
+                flips += check_tie_flips(ref, before, rec, b0, b1, r2)
+                total += 2 << N
+    assert flips <= max(4, total // 1000)
+
+
+def test_tiny_magnitudes_enter_the_range(q):
+    # amplitudes far below 1e-19 square to zero in FP32; the device takes
+    # their magnitude from the scaled components, so r0 (the smallest |z| in
+    # (0, 1)) and the codes follow the FP64 definition
+    N = 10
+    g = np.random.default_rng(4)
+    z = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
+    z /= np.linalg.norm(z)
+    tiny = [3e-21, 1e-25, 2e-30]
+    # tiny values on pairs (i, i + 1) so that H on qubit 0 keeps them tiny
+    for k, t in enumerate(tiny):
+        z[2 * k] = t
+        z[2 * k + 1] = 0.5 * t * (1 + 1j)
+    a = a2.AState.from_complex(N, z)
+    assert a.r0 < 1e-29
+    rec = ("H", (0,), ())
+    ref = circuit.run_adapt2(a.copy(), [rec])
+    b0, b1, r = gpu_run(q, a, [rec])
+    assert ref.r0 < 1e-29
+    assert abs(r[0] - ref.r0) <= 1e-5 * ref.r0
+    check_tie_flips(ref, a, rec, b0, b1, r)
+
+
+@pytest.mark.parametrize("N", [6, 13, 20])
+def test_overlap_across_encodings(q, N):
+    recs = wl.layered_circuit(N, 2, seed=N)
+    with q.Sim(N, "c128") as e, q.Sim(N, "c64") as f, q.Sim(N, "adapt2") as a:
+        e.circuit_run(recs, mode=1)
+        f.circuit_run(recs, mode=1)
+        a.circuit_run(recs, mode=0)
+        ve = e.copy_out()
+        vf = f.copy_out().astype(np.complex128)
+        w, r = a.copy_out()
+        va = a2.decode(*a2.unpack(w), r[0], r[1])
+        for x, vx in ((e, ve), (f, vf), (a, va)):
+            for y, vy in ((e, ve), (f, vf), (a, va)):
+                ov, d2 = x.overlap(y)
+                # the device decodes adaptive words with FP32 tables (this
+                # test in FP64): those pairs agree to FP32 precision
+                tol = 1e-6 if (x is a or y is a) else 1e-12
+                assert abs(ov - np.vdot(vx, vy)) <= tol * (1 + abs(np.vdot(vx, vy)))
+                assert abs(d2 - float(np.sum(np.abs(vx - vy) ** 2))) <= tol * (1 + d2)
