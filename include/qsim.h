@@ -519,21 +519,40 @@ typedef struct {
 } qs_request;
 typedef struct {
   size_t mem_budget;      /* bytes of device memory for resident states and gate lists */
-  int quantum;            /* gates per request per tick (<= 0: 64) */
+  int quantum;            /* gates per request per tick / work item (<= 0: 64) */
   int max_small;          /* small states per batched launch (<= 0: 4096) */
   int nstreams;           /* streams for larger states (<= 0: 4, at most 16) */
   int small_max_n;        /* largest N of the batched path (<= 0: 14) */
+  int persistent;         /* 1: persistent kernel and device work queue (below); 0: ticks */
+  int persistent_ctas;    /* CTAs of the persistent kernel (<= 0: half the SMs) */
+  double device_wait_ms;  /* longest wait of a persistent CTA for work (<= 0: 200 ms) */
+  int large_quantum;      /* gates per chunk of a larger state (<= 0: quantum) */
 } qs_serve_config;
 typedef struct {
   int completed, ticks, max_active;
   double wall_s;          /* from start to the last completion */
-  double busy_s;          /* time spent in ticks (at least one request active) */
+  double busy_s;          /* time with at least one request active */
   uint64_t launches;      /* kernels launched */
   size_t peak_bytes;      /* peak pool usage */
+  uint64_t work_items;    /* persistent mode: work items the device took from the queue */
+  int idle_exits;         /* persistent mode: CTAs that ended a bounded wait without work */
+  int relaunches;         /* persistent mode: launches of the persistent kernel */
 } qs_serve_stats;
 /* Serve n requests (sorted by arrival) in real time on the current device.
  * Rejects malformed requests and requests that cannot fit the budget before
- * anything runs.  Allocates the budget once (plus small staging buffers). */
+ * anything runs.  Allocates the budget once (plus small staging buffers).
+ *
+ * Persistent mode (cfg->persistent = 1): the small states run in a
+ * persistent kernel whose CTAs take work items (one state, its next chunk of
+ * up to `quantum` gates) from a queue in host-mapped memory as the host
+ * publishes them, each state held in shared memory for its chunk; every wait
+ * of a CTA for work is bounded by device_wait_ms (%globaltimer), after which
+ * the CTA ends (counted in idle_exits) and the host launches the kernel
+ * again when new work arrives.  Larger states run their chunks of
+ * large_quantum gates through the tile planner on their own streams, each
+ * advanced as soon as its previous chunk completes (no global tick), so all
+ * of this overlaps on the device.  The host gives up with QS_ETIMEOUT when
+ * nothing completes for 60 s. */
 qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* cfg, qs_serve_stats* stats);
 
 /* ---- raw state access (parity dumps) ------------------------------------- */

@@ -707,8 +707,10 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
     int feat = 0;
     for (int i = 0; i < P.nops; ++i) {
       const TOp& o = P.ops[i];
-      if ((o.type == T_LANE || o.type == T_REG) && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0) feat |= FEAT_SWAP;
-      if ((o.type == T_REG || o.type == T_LANE) && (o.kind == GK_REAL || o.kind == GK_BFLY)) feat |= FEAT_HAD;
+      const bool swap = o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0;
+      if (o.type == T_LANE && swap) feat |= FEAT_SWAP;
+      if ((o.type == T_REG && swap) || ((o.type == T_REG || o.type == T_LANE) && (o.kind == GK_REAL || o.kind == GK_BFLY)))
+        feat |= FEAT_HAD;
     }
     const size_t smem = ((size_t)8 << P.b) + tile_smem_header(5);
     auto go = [&](auto kern) -> qs_status {

@@ -72,6 +72,108 @@ __global__ void __launch_bounds__(STPB) k_serve_small(const SmallEntry* __restri
   }
 }
 
+// ---- persistent mode -------------------------------------------------------------------
+// A work item: one small state and its next gate chunk.  Items live in a ring
+// in host-mapped memory; the host fills an item, then publishes it by
+// raising `tail` (release); a CTA claims the oldest published item with a
+// CAS on the device counter `head`, runs it with the state in shared memory,
+// writes the results (for a final chunk) and marks the ring slot done with
+// the item's number (release, system scope).
+struct WorkItem {
+  float2* state;
+  const BGate<float>* gates;
+  double* res;                 // host-mapped: [norm, P1(0..N-1)] for a final chunk
+  int N, g0, g1, fresh, final_;
+  int pad;
+};
+struct QueueCtl {              // host-mapped
+  unsigned long long tail;     // items published
+  unsigned long long stop;     // nonzero: CTAs end at their next wait
+  unsigned long long done[1];  // [ring]: number + 1 of the item finished in the slot
+};
+
+__device__ __forceinline__ unsigned long long ld_acq_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(STPB) k_serve_persist(const WorkItem* ring, unsigned ring_n, QueueCtl* ctl,
+                                                        unsigned long long* head, unsigned long long wait_ns,
+                                                        unsigned int* idle_exits, unsigned long long* taken) {
+  extern __shared__ unsigned char smraw[];
+  Cx<float>* st = (Cx<float>*)smraw;
+  __shared__ double red[32];
+  __shared__ long long my;
+  __shared__ WorkItem it;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // claim the oldest published item; wait at most wait_ns for one
+      long long got = -1;
+      const unsigned long long t0 = gtimer();
+      for (;;) {
+        const unsigned long long h = atomicAdd(head, 0ull);
+        const unsigned long long t = ld_acq_sys(&ctl->tail);
+        if (h < t) {
+          if (atomicCAS(head, h, h + 1) == h) { got = (long long)h; break; }
+          continue;
+        }
+        if (ld_acq_sys(&ctl->stop) || gtimer() - t0 > wait_ns) break;
+        __nanosleep(1000);
+      }
+      my = got;
+      if (got >= 0) {
+        it = ring[got % ring_n];
+        atomicAdd(taken, 1ull);
+      } else {
+        atomicAdd(idle_exits, 1u);
+      }
+    }
+    __syncthreads();
+    if (my < 0) return;
+    const int n = 1 << it.N;
+    if (it.fresh) {
+      for (int i = threadIdx.x; i < n; i += STPB) st[i] = cx<float>(i == 0 ? 1.f : 0.f, 0.f);
+    } else {
+      for (int i = threadIdx.x; i < n; i += STPB) { float2 a = it.state[i]; st[i] = cx<float>(a.x, a.y); }
+    }
+    __syncthreads();
+    for (int k = it.g0; k < it.g1; ++k) {
+      apply_gate_range<float>(st, it.N, it.gates[k], threadIdx.x, STPB);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += STPB) it.state[i] = make_float2(st[i].x, st[i].y);
+    if (it.final_) {
+      for (int q = -1; q < it.N; ++q) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < n; i += STPB)
+          if (q < 0 || ((i >> q) & 1)) acc += (double)st[i].x * st[i].x + (double)st[i].y * st[i].y;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double r = 0.0;
+          for (int w = 0; w < STPB / 32; ++w) r += red[w];
+          it.res[q + 1] = r;
+        }
+        __syncthreads();
+      }
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) st_rel_sys(&ctl->done[my % ring_n], (unsigned long long)my + 1);
+    __syncthreads();
+  }
+}
+
 // first-fit allocator over [0, size) with 256-byte granules
 class Pool {
  public:
@@ -122,6 +224,9 @@ struct Active {
 
 }  // namespace
 
+static qs_status serve_persistent(qs_request* reqs, int n, const qs_serve_config* cfg, qs_serve_stats* stats,
+                                  int small_max, int quantum, int nstreams, size_t budget);
+
 extern "C" qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* cfg, qs_serve_stats* stats) {
   if (!reqs || n < 0 || !cfg) { qs_set_error("serve_run: null argument"); return QS_EINVAL; }
   const int small_max = cfg->small_max_n > 0 ? (cfg->small_max_n < 14 ? cfg->small_max_n : 14) : 14;
@@ -151,6 +256,8 @@ extern "C" qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* c
       if (!(unitarity_defect(g.u, 2) <= 1e-10)) { qs_set_error("serve_run: request %d gate %d not unitary", i, k); return QS_ENOTUNITARY; }
     }
   }
+  if (stats) memset(stats, 0, sizeof *stats);
+  if (cfg->persistent) return serve_persistent(reqs, n, cfg, stats, small_max, quantum, nstreams, budget);
   // resources
   unsigned char* pool_base = nullptr;
   QS_CUDA(cudaMalloc(&pool_base, budget));
@@ -315,6 +422,285 @@ extern "C" qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* c
     stats->launches = qs_kernel_launches() - launches0;
     stats->peak_bytes = pool.peak();
     stats->max_active = max_active;
+  }
+  return st;
+}
+
+// =========================================================================================
+// persistent mode: event-driven host loop around the persistent kernel
+// =========================================================================================
+namespace {
+struct PActive {
+  int id;
+  bool small;
+  size_t off, bytes, goff, gbytes;
+  int next;                 // next gate to enqueue
+  bool fresh;
+  long long item;           // small: number of the item in flight, -1 if none
+  int pending_g1;           // small: end of the chunk in flight
+  qs_sim* sim;              // large
+  int stream;
+  cudaEvent_t ev;           // large: end of the chunk in flight
+  bool in_flight;
+};
+}  // namespace
+
+static qs_status serve_persistent(qs_request* reqs, int n, const qs_serve_config* cfg, qs_serve_stats* stats,
+                                  int small_max, int quantum, int nstreams, size_t budget) {
+  const unsigned R = 4096;                      // ring slots: at most R small states in flight
+  const int res_stride = 16;                    // doubles per result slot (N <= 14: 1 + 14)
+  const int lq = cfg->large_quantum > 0 ? cfg->large_quantum : quantum;
+  const double wait_ms = cfg->device_wait_ms > 0 ? cfg->device_wait_ms : 200.0;
+  int dev = 0, sms = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int ctas = cfg->persistent_ctas > 0 ? cfg->persistent_ctas : (sms / 2 > 0 ? sms / 2 : 1);
+  // resources (released at the end whatever happens)
+  unsigned char* pool_base = nullptr;
+  WorkItem* ring_h = nullptr;
+  QueueCtl* ctl_h = nullptr;
+  double* res_h = nullptr;
+  unsigned long long* dcount = nullptr;   // head, taken
+  unsigned int* didle = nullptr;
+  std::vector<cudaStream_t> streams(nstreams + 1, nullptr);
+  cudaEvent_t kev = nullptr;
+  std::vector<PActive> active;
+  qs_status st = QS_OK;
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == QS_OK) {
+      qs_set_error("serve_run: %s: %s", what, cudaGetErrorString(e));
+      st = QS_ECUDA;
+    }
+    return st == QS_OK;
+  };
+  cu(cudaMalloc(&pool_base, budget), "pool");
+  cu(cudaHostAlloc(&ring_h, sizeof(WorkItem) * R, cudaHostAllocMapped), "ring");
+  cu(cudaHostAlloc(&ctl_h, sizeof(QueueCtl) + sizeof(unsigned long long) * (R - 1), cudaHostAllocMapped), "queue");
+  cu(cudaHostAlloc(&res_h, sizeof(double) * res_stride * R, cudaHostAllocMapped), "results");
+  cu(cudaMalloc(&dcount, 2 * sizeof(unsigned long long)), "counters");
+  cu(cudaMalloc(&didle, sizeof(unsigned int)), "counters");
+  for (auto& x : streams) cu(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "stream");
+  cu(cudaEventCreateWithFlags(&kev, cudaEventDisableTiming), "event");
+  WorkItem* ring_d = nullptr;
+  QueueCtl* ctl_d = nullptr;
+  double* res_d = nullptr;
+  if (st == QS_OK) {
+    memset(ctl_h, 0, sizeof(QueueCtl) + sizeof(unsigned long long) * (R - 1));
+    cu(cudaHostGetDevicePointer((void**)&ring_d, ring_h, 0), "mapping");
+    cu(cudaHostGetDevicePointer((void**)&ctl_d, ctl_h, 0), "mapping");
+    cu(cudaHostGetDevicePointer((void**)&res_d, res_h, 0), "mapping");
+    cu(cudaMemsetAsync(dcount, 0, 2 * sizeof(unsigned long long), streams[0]), "memset");
+    cu(cudaMemsetAsync(didle, 0, sizeof(unsigned int), streams[0]), "memset");
+    cu(cudaFuncSetAttribute(k_serve_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << 14), "attribute");
+    cu(cudaStreamSynchronize(streams[0]), "sync");
+  }
+  Pool pool(budget);
+  const uint64_t launches0 = qs_kernel_launches();
+  const auto t0 = std::chrono::steady_clock::now();
+  auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+  unsigned long long published = 0, finished_items = 0;
+  bool kernel_live = false;
+  int relaunches = 0, completed = 0, max_active = 0, nsmall = 0, next_arrival = 0;
+  double busy = 0.0, last_progress = 0.0, busy_from = -1.0;
+  std::vector<BGate<float>> hg;
+  auto launch_kernel = [&]() {
+    k_serve_persist<<<ctas, STPB, 8 << 14, streams[0]>>>(ring_d, R, ctl_d, dcount, (unsigned long long)(wait_ms * 1e6),
+                                                        didle, dcount + 1);
+    qs_count_launch();
+    cu(cudaGetLastError(), "persistent launch");
+    cu(cudaEventRecord(kev, streams[0]), "event");
+    kernel_live = true;
+    ++relaunches;
+  };
+  auto publish = [&](PActive& a) {
+    const qs_request& r = reqs[a.id];
+    const unsigned long long k = published;
+    WorkItem& w = ring_h[k % R];
+    w.state = (float2*)(pool_base + a.off);
+    w.gates = (const BGate<float>*)(pool_base + a.goff);
+    w.res = res_d + (size_t)res_stride * (k % R);
+    w.N = r.N;
+    w.g0 = a.next;
+    w.g1 = std::min(r.ngates, a.next + quantum);
+    w.fresh = a.fresh ? 1 : 0;
+    w.final_ = (w.g1 == r.ngates) ? 1 : 0;
+    a.item = (long long)k;
+    a.pending_g1 = w.g1;
+    published = k + 1;
+    __atomic_store_n(&ctl_h->tail, published, __ATOMIC_RELEASE);
+  };
+  while (st == QS_OK && completed < n) {
+    bool progress = false;
+    const double tnow = now_s();
+    // admission, oldest first, while the state and its gate list fit
+    while (st == QS_OK && next_arrival < n && reqs[next_arrival].arrival_s <= tnow) {
+      qs_request& r = reqs[next_arrival];
+      PActive a;
+      memset(&a, 0, sizeof a);
+      a.id = next_arrival;
+      a.small = r.N <= small_max;
+      if (a.small && nsmall >= (int)R) break;
+      a.bytes = (size_t)8 << r.N;
+      a.gbytes = a.small ? (size_t)r.ngates * sizeof(BGate<float>) : 0;
+      if (!pool.alloc(a.bytes, &a.off)) break;
+      if (a.small && a.gbytes && !pool.alloc(a.gbytes, &a.goff)) { pool.release(a.off, a.bytes); break; }
+      a.fresh = true;
+      a.item = -1;
+      a.stream = (int)(next_arrival % nstreams) + 1;
+      if (a.small) {
+        hg.resize(r.ngates);
+        for (int k = 0; k < r.ngates; ++k) {
+          const qs_gate& g = r.gates[k];
+          BGate<float>& o = hg[k];
+          o.nc = g.nc; o.c0 = g.controls[0]; o.c1 = g.controls[1]; o.t = g.target;
+          for (int j = 0; j < 8; ++j) o.u[j] = (float)g.u[j];
+        }
+        if (r.ngates) cu(cudaMemcpy(pool_base + a.goff, hg.data(), a.gbytes, cudaMemcpyHostToDevice), "gate upload");
+        ++nsmall;
+      } else {
+        qs_status s2 = sim_create_in(r.N, QS_C64, pool_base + a.off, a.bytes, (void*)streams[a.stream], &a.sim);
+        if (s2 != QS_OK) { st = s2; break; }
+        cu(cudaEventCreateWithFlags(&a.ev, cudaEventDisableTiming), "event");
+      }
+      r.admit_s = tnow;
+      active.push_back(a);
+      ++next_arrival;
+      progress = true;
+    }
+    if (st != QS_OK) break;
+    max_active = std::max(max_active, (int)active.size());
+    if (!active.empty() && busy_from < 0) busy_from = tnow;
+    // advance every request whose previous work finished
+    std::vector<PActive> keep;
+    keep.reserve(active.size());
+    for (auto& a : active) {
+      qs_request& r = reqs[a.id];
+      bool done_req = false;
+      if (a.small) {
+        if (a.item >= 0) {
+          const unsigned long long d = __atomic_load_n(&ctl_h->done[a.item % R], __ATOMIC_ACQUIRE);
+          if (d == (unsigned long long)a.item + 1) {
+            ++finished_items;
+            progress = true;
+            a.fresh = false;
+            a.next = a.pending_g1;
+            if (a.next == r.ngates) {
+              const double* res = res_h + (size_t)res_stride * (a.item % R);
+              r.norm = res[0];
+              for (int q = 0; q < r.N; ++q) r.qz[q] = res[1 + q];
+              done_req = true;
+            }
+            a.item = -1;
+          }
+        }
+        if (!done_req && a.item < 0) {
+          publish(a);
+          progress = true;
+        }
+      } else {
+        if (a.in_flight) {
+          const cudaError_t q = cudaEventQuery(a.ev);
+          if (q == cudaErrorNotReady) { keep.push_back(a); continue; }
+          if (!cu(q, "large chunk")) break;
+          a.in_flight = false;
+          progress = true;
+        }
+        if (a.next < r.ngates) {
+          const int g1 = std::min(r.ngates, a.next + lq);
+          qs_status s2 = circuit_run(a.sim, r.gates + a.next, g1 - a.next, 1, nullptr);
+          if (s2 != QS_OK) { st = s2; break; }
+          a.next = g1;
+          cu(cudaEventRecord(a.ev, streams[a.stream]), "event");
+          a.in_flight = true;
+        } else {
+          std::vector<double> qx(r.N), qy(r.N);
+          qs_status s2 = expect_xyz(a.sim, qx.data(), qy.data(), r.qz);
+          if (s2 == QS_OK) s2 = sim_norm(a.sim, &r.norm);
+          if (s2 != QS_OK) { st = s2; break; }
+          sim_destroy(a.sim);
+          a.sim = nullptr;
+          cudaEventDestroy(a.ev);
+          done_req = true;
+        }
+      }
+      if (done_req) {
+        r.finish_s = now_s();
+        pool.release(a.off, a.bytes);
+        if (a.gbytes) pool.release(a.goff, a.gbytes);
+        if (a.small) --nsmall;
+        ++completed;
+        progress = true;
+      } else {
+        keep.push_back(a);
+      }
+    }
+    if (st != QS_OK) break;
+    active.swap(keep);
+    if (active.empty() && busy_from >= 0) { busy += now_s() - busy_from; busy_from = -1.0; }
+    // the persistent kernel: (re)launch when items wait and its CTAs have ended
+    if (kernel_live) {
+      const cudaError_t q = cudaEventQuery(kev);
+      if (q == cudaSuccess) kernel_live = false;
+      else if (q != cudaErrorNotReady) { cu(q, "persistent kernel"); break; }
+    }
+    if (!kernel_live && published > finished_items) launch_kernel();
+    if (progress) {
+      last_progress = now_s();
+    } else {
+      if (now_s() - last_progress > 60.0) {
+        qs_set_error("serve_run: no progress for 60 s");
+        st = QS_ETIMEOUT;
+        break;
+      }
+      if (active.empty() && next_arrival < n) {
+        const double w = reqs[next_arrival].arrival_s - now_s();
+        if (w > 0) std::this_thread::sleep_for(std::chrono::duration<double>(w < 1e-3 ? w : 1e-3));
+      } else {
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      }
+    }
+  }
+  if (busy_from >= 0) busy += now_s() - busy_from;
+  const double wall = now_s();
+  // stop the persistent CTAs (they see the flag within one poll) and wait,
+  // bounded, for the kernel and the streams
+  if (ctl_h) __atomic_store_n(&ctl_h->stop, 1ull, __ATOMIC_RELEASE);
+  if (kernel_live) {
+    const auto ts = std::chrono::steady_clock::now();
+    while (cudaEventQuery(kev) == cudaErrorNotReady &&
+           std::chrono::steady_clock::now() - ts < std::chrono::seconds(30))
+      std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+  unsigned long long taken = 0;
+  unsigned int idle = 0;
+  if (dcount) cudaMemcpy(&taken, dcount + 1, sizeof taken, cudaMemcpyDeviceToHost);
+  if (didle) cudaMemcpy(&idle, didle, sizeof idle, cudaMemcpyDeviceToHost);
+  for (auto& x : streams)
+    if (x) cudaStreamSynchronize(x);
+  for (auto& a : active) {
+    if (a.sim) sim_destroy(a.sim);
+    if (!a.small && a.ev) cudaEventDestroy(a.ev);
+  }
+  for (auto& x : streams)
+    if (x) cudaStreamDestroy(x);
+  if (kev) cudaEventDestroy(kev);
+  cudaFree(pool_base);
+  cudaFree(dcount);
+  cudaFree(didle);
+  cudaFreeHost(ring_h);
+  cudaFreeHost(ctl_h);
+  cudaFreeHost(res_h);
+  if (stats) {
+    stats->completed = completed;
+    stats->ticks = 0;
+    stats->wall_s = wall;
+    stats->busy_s = busy;
+    stats->launches = qs_kernel_launches() - launches0;
+    stats->peak_bytes = pool.peak();
+    stats->max_active = max_active;
+    stats->work_items = taken;
+    stats->idle_exits = (int)idle;
+    stats->relaunches = relaunches;
   }
   return st;
 }

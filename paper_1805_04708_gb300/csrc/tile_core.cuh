@@ -345,7 +345,7 @@ __host__ __device__ constexpr unsigned tile_smem_header(int RB) {
 
 // FEAT: which specialised complex64 paths the pass needs (bit 0: swaps, bit 1:
 // Hadamard-shaped); passes without them run a smaller kernel.
-constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_SWAP: X-type exchanges; FEAT_HAD: real-matrix path (packed FP32x2)
+constexpr int FEAT_SWAP = 1, FEAT_HAD = 2;   // FEAT_SWAP: lane exchanges; FEAT_HAD: real-matrix path (packed FP32x2)
 
 // 16-byte global -> shared copies that bypass registers (LDGSTS), so the next
 // tile's loads are in flight while the current tile is computed and stored.
@@ -551,14 +551,20 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
             // of X, Y, CNOT, TOFFOLI)
             // (a register-slot swap as renames makes the register allocation
             // spill at 128 registers; swaps on register slots stay dense)
-            if ((FEAT & FEAT_SWAP) && st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0) {
-              // X-type (X, CNOT, TOFFOLI): the pair only exchanges values
+            const bool pure_swap = st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0;
+            if (Prog::kN >= 0 && pure_swap && st.gmask == 0 && st.tmask == 0) {
+              // X-type (X, CNOT, TOFFOLI) with no condition decided at run
+              // time: in a compiled pass the exchange is a renaming of
+              // registers and costs no instruction.  (Under a per-tile or
+              // per-thread condition, and in the interpreter, a swap takes
+              // the packed real-matrix path below: renames there turn into
+              // moves and spills.)
               OpSwapC<R> f;
               reg_op<R, RB>(v, st.a, st.smask, f);
             } else if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
               OpBflyF f;
               reg_op<R, RB>(v, st.a, st.smask, f);
-            } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY)) {
+            } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY || pure_swap)) {
               OpRealF f;
               f.u00 = make_float2(o.uf[0], o.uf[0]); f.u01 = make_float2(o.uf[2], o.uf[2]);
               f.u10 = make_float2(o.uf[4], o.uf[4]); f.u11 = make_float2(o.uf[6], o.uf[6]);

@@ -50,13 +50,16 @@ class qs_request(ctypes.Structure):
 
 class qs_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_size_t), ("quantum", ctypes.c_int), ("max_small", ctypes.c_int),
-                ("nstreams", ctypes.c_int), ("small_max_n", ctypes.c_int)]
+                ("nstreams", ctypes.c_int), ("small_max_n", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("persistent_ctas", ctypes.c_int), ("device_wait_ms", ctypes.c_double),
+                ("large_quantum", ctypes.c_int)]
 
 
 class qs_serve_stats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int), ("ticks", ctypes.c_int), ("max_active", ctypes.c_int),
                 ("wall_s", ctypes.c_double), ("busy_s", ctypes.c_double), ("launches", ctypes.c_uint64),
-                ("peak_bytes", ctypes.c_size_t)]
+                ("peak_bytes", ctypes.c_size_t), ("work_items", ctypes.c_uint64), ("idle_exits", ctypes.c_int),
+                ("relaunches", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -658,10 +661,12 @@ class Batch:
         _check(_lib.batch_copy_in(self._h, _P(a.ctypes.data), self.nbytes))
 
 
-def serve(requests, mem_budget, quantum=64, nstreams=4, small_max_n=14, max_small=4096):
+def serve(requests, mem_budget, quantum=64, nstreams=4, small_max_n=14, max_small=4096, persistent=False,
+          persistent_ctas=0, device_wait_ms=0.0, large_quantum=0):
     """Run the serving loop.  requests: list of dicts with arrival (s), N and
-    records (gate records).  Returns (results, stats): per request a dict with
-    qz, norm, admit_s, finish_s, latency_s."""
+    records (gate records).  persistent: the persistent-kernel mode (device
+    work queue, bounded device waits).  Returns (results, stats): per request
+    a dict with qz, norm, admit_s, finish_s, latency_s."""
     n = len(requests)
     reqs = (qs_request * max(1, n))()
     keep = []
@@ -674,7 +679,8 @@ def serve(requests, mem_budget, quantum=64, nstreams=4, small_max_n=14, max_smal
         reqs[i].ngates = ng
         reqs[i].gates = ctypes.cast(arr, ctypes.POINTER(qs_gate))
         reqs[i].qz = qz.ctypes.data_as(_D)
-    cfg = qs_serve_config(int(mem_budget), int(quantum), int(max_small), int(nstreams), int(small_max_n))
+    cfg = qs_serve_config(int(mem_budget), int(quantum), int(max_small), int(nstreams), int(small_max_n),
+                          1 if persistent else 0, int(persistent_ctas), float(device_wait_ms), int(large_quantum))
     st = qs_serve_stats()
     _check(_lib.serve_run(reqs, n, ctypes.byref(cfg), ctypes.byref(st)))
     out = []
@@ -682,7 +688,8 @@ def serve(requests, mem_budget, quantum=64, nstreams=4, small_max_n=14, max_smal
         out.append(dict(qz=keep[i][1].copy(), norm=reqs[i].norm, admit_s=reqs[i].admit_s,
                         finish_s=reqs[i].finish_s, latency_s=reqs[i].finish_s - reqs[i].arrival_s))
     stats = dict(completed=st.completed, ticks=st.ticks, max_active=st.max_active, wall_s=st.wall_s,
-                 busy_s=st.busy_s, launches=st.launches, peak_bytes=st.peak_bytes)
+                 busy_s=st.busy_s, launches=st.launches, peak_bytes=st.peak_bytes, work_items=st.work_items,
+                 idle_exits=st.idle_exits, relaunches=st.relaunches)
     return out, stats
 
 
