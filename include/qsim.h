@@ -485,9 +485,27 @@ qs_status batch_run(qs_batch* b);
 /* Capture one batch_run into a CUDA graph that later batch_run calls replay. */
 qs_status batch_capture(qs_batch* b);
 /* Time the launch layouts (one CTA per state, one warp per state for N <= 9)
- * and CTA sizes on the current gate lists and keep the fastest; the states
- * are restored afterwards.  Outputs may be NULL. */
+ * and CTA sizes of the per-gate kernels, and the fused configurations of
+ * batch_set_tuning (fusion width 1..4, 2^0..2^5 states per CTA, 128 / 256 /
+ * 512 threads), on the current gate lists, and keep the fastest; the states
+ * are restored afterwards.  layout (0 / 1 for the per-gate kernels, 2 for
+ * the fused kernel), threads and the best time may be NULL;
+ * batch_get_tuning reports the whole choice. */
 qs_status batch_autotune(qs_batch* b, int* layout, int* threads, float* best_ms);
+/* Kernel configuration of batch_run (the batching has no counterpart in the
+ * paper).  fuse_k = 0: one shared-memory step per gate (the kernels of
+ * batch_autotune's layouts: tile_bits = N gives one CTA per state, tile_bits
+ * > N one warp per state); fuse_k = 1..4: each state's consecutive gates are
+ * composed on the host in FP64 into dense blocks on at most fuse_k qubits (a
+ * gate wider than fuse_k is its own block; the block's matrix is rounded
+ * once to the state's precision, so results equal the gate-by-gate product
+ * up to rounding) and applied as 2^m x 2^m products in shared memory, with
+ * 2^(tile_bits - N) states per CTA (tile_bits from N to N + 5, every state
+ * getting at least 32 threads, shared memory within 200 KB).  threads: the
+ * CTA size.  Invalid combinations give QS_EINVAL.  batch_autotune times
+ * these configurations as well and keeps the fastest. */
+qs_status batch_set_tuning(qs_batch* b, int fuse_k, int tile_bits, int threads);
+qs_status batch_get_tuning(const qs_batch* b, int* fuse_k, int* tile_bits, int* threads);
 /* <Phi|Phi> of every state (host, nstates doubles), FP64. */
 qs_status batch_norms(qs_batch* b, double* out);
 /* Raw amplitudes of all states (nstates * 2^N * 8 or 16 bytes), host. */

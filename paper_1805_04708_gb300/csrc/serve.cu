@@ -106,6 +106,30 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
+// A persistent CTA may take chunk k + 1 of a state whose chunk k another SM
+// wrote, and a pool region may hold a new request's gates: everything such a
+// CTA reads that others wrote during the kernel's lifetime is loaded through
+// L2 (ld.global.cg), never from this SM's L1, which is not coherent with the
+// other SMs' writes.
+__device__ __forceinline__ BGate<float> gate_cg(const BGate<float>* p) {
+  static_assert(sizeof(BGate<float>) == 48, "gate record layout");
+  const int4* q = (const int4*)p;
+  int4 w[3] = {__ldcg(q), __ldcg(q + 1), __ldcg(q + 2)};
+  BGate<float> g;
+  memcpy(&g, w, sizeof g);
+  return g;
+}
+__device__ __forceinline__ WorkItem item_cg(const WorkItem* p) {
+  static_assert(sizeof(WorkItem) % 16 == 0, "work item layout");
+  WorkItem it;
+  const int4* q = (const int4*)p;
+  int4 w[sizeof(WorkItem) / 16];
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(WorkItem) / 16); ++i) w[i] = __ldcg(q + i);
+  memcpy(&it, w, sizeof it);
+  return it;
+}
+
 __global__ void __launch_bounds__(STPB) k_serve_persist(const WorkItem* ring, unsigned ring_n, QueueCtl* ctl,
                                                         unsigned long long* head, unsigned long long wait_ns,
                                                         unsigned int* idle_exits, unsigned long long* taken) {
@@ -131,7 +155,7 @@ __global__ void __launch_bounds__(STPB) k_serve_persist(const WorkItem* ring, un
       }
       my = got;
       if (got >= 0) {
-        it = ring[got % ring_n];
+        it = item_cg(ring + got % ring_n);
         atomicAdd(taken, 1ull);
       } else {
         atomicAdd(idle_exits, 1u);
@@ -143,14 +167,14 @@ __global__ void __launch_bounds__(STPB) k_serve_persist(const WorkItem* ring, un
     if (it.fresh) {
       for (int i = threadIdx.x; i < n; i += STPB) st[i] = cx<float>(i == 0 ? 1.f : 0.f, 0.f);
     } else {
-      for (int i = threadIdx.x; i < n; i += STPB) { float2 a = it.state[i]; st[i] = cx<float>(a.x, a.y); }
+      for (int i = threadIdx.x; i < n; i += STPB) { float2 a = __ldcg(it.state + i); st[i] = cx<float>(a.x, a.y); }
     }
     __syncthreads();
     for (int k = it.g0; k < it.g1; ++k) {
-      apply_gate_range<float>(st, it.N, it.gates[k], threadIdx.x, STPB);
+      apply_gate_range<float>(st, it.N, gate_cg(it.gates + k), threadIdx.x, STPB);
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < n; i += STPB) it.state[i] = make_float2(st[i].x, st[i].y);
+    for (int i = threadIdx.x; i < n; i += STPB) __stcg(it.state + i, make_float2(st[i].x, st[i].y));
     if (it.final_) {
       for (int q = -1; q < it.N; ++q) {
         double acc = 0.0;

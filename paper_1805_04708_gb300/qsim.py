@@ -130,6 +130,8 @@ _SIGS = {
     "batch_copy_out": (_I, [_P, _P, ctypes.c_size_t]),
     "batch_copy_in": (_I, [_P, _P, ctypes.c_size_t]),
     "batch_info": (_I, [_P, _IP, _IP, ctypes.POINTER(_P)]),
+    "batch_set_tuning": (_I, [_P, _I, _I, _I]),
+    "batch_get_tuning": (_I, [_P, _IP, _IP, _IP]),
     "serve_run": (_I, [ctypes.POINTER(qs_request), _I, ctypes.POINTER(qs_serve_config), ctypes.POINTER(qs_serve_stats)]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -638,6 +640,16 @@ class Batch:
         lay, th, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0)
         _check(_lib.batch_autotune(self._h, ctypes.byref(lay), ctypes.byref(th), ctypes.byref(ms)))
         return lay.value, th.value, ms.value
+
+    def set_tuning(self, fuse_k, tile_bits, threads):
+        """Kernel configuration (see batch_set_tuning)."""
+        _check(_lib.batch_set_tuning(self._h, int(fuse_k), int(tile_bits), int(threads)))
+
+    def tuning(self):
+        """(fuse_k, tile_bits, threads) of the current configuration."""
+        k, b, t = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib.batch_get_tuning(self._h, ctypes.byref(k), ctypes.byref(b), ctypes.byref(t)))
+        return k.value, b.value, t.value
 
     def info(self):
         lay, th, p = ctypes.c_int(0), ctypes.c_int(0), _P()

@@ -52,8 +52,11 @@ def test_batch_graph_and_autotune(q, enc, N):
     with q.Batch(N, enc, ns) as b:
         b.set_circuits(circs)
         layout, threads, ms = b.autotune()
-        assert layout in (0, 1) and threads in (64, 128, 256, 512, 1024) and ms > 0
-        assert b.info()[:2] == (layout, threads)
+        assert layout in (0, 1, 2) and threads in (64, 128, 256, 512, 1024) and ms > 0
+        fk, tb, th = b.tuning()
+        assert th == threads and (fk > 0) == (layout == 2)
+        if layout < 2:
+            assert b.info()[:2] == (layout, threads)
         b.capture()
         b.run()          # graph replay: one pass of every circuit
         b.run()          # and a second one
@@ -61,6 +64,39 @@ def test_batch_graph_and_autotune(q, enc, N):
     for s in range(0, ns, 7):
         ref = circuit.run(sv.zero_state(N), N, circs[s] + circs[s])
         assert np.max(np.abs(got[s] - ref)) <= TOL[enc] * 2
+
+
+@pytest.mark.parametrize("enc,N", [("c64", 5), ("c64", 10), ("c64", 14), ("c128", 6), ("c128", 12)])
+def test_batch_fused_configurations(q, enc, N):
+    # every fusion width and several states-per-CTA tilings against the
+    # oracle, gate lists of different lengths per state (with TOFFOLI and
+    # controlled gates, so blocks of 3 and 4 qubits occur), and a graph replay
+    ns = 19
+    circs = [wl.random_mixed_circuit(N, 4 + 9 * (s % 4), seed=77 * N + s) for s in range(ns)]
+    refs = [circuit.run(sv.zero_state(N), N, c) for c in circs]
+    with q.Batch(N, enc, ns) as b:
+        b.set_circuits(circs)
+        tried = 0
+        for k in (1, 2, 3, 4):
+            for tb, th in ((N, 128), (N + 1, 256), (N + 2, 512), (N + 3, 512)):
+                try:
+                    b.set_tuning(k, tb, th)
+                except q.QSError:
+                    continue   # more shared memory or fewer threads per state than allowed
+                tried += 1
+                b.reset()
+                b.run()
+                got = b.copy_out()
+                for st in range(ns):
+                    assert np.max(np.abs(got[st] - refs[st])) <= TOL[enc] * 4, (k, tb, th, st)
+        assert tried >= 4
+        b.set_tuning(3, N, 256)
+        b.capture()
+        b.reset()
+        b.run()
+        got = b.copy_out()
+        for st in range(ns):
+            assert np.max(np.abs(got[st] - refs[st])) <= TOL[enc] * 4
 
 
 def test_batch_errors(q):
