@@ -382,8 +382,9 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
     torch.cuda.empty_cache()
 
     # dense fused k-qubit gates (k = 2..5) on the k lowest qubits: tcgen05
-    # (k >= 3) and mma.sync tensor-core kernels (3xTF32), against the
-    # CUDA-core kernel (qubits 1..k)
+    # (k >= 3) and mma.sync tensor-core kernels (3xTF32); on the spread
+    # qubits 3, 9, 17, 22, 29: the CUDA-core kernel, and the tensor cores
+    # after moving the qubits to the low bits (and back)
     s64 = qsim.Sim(N, "c64", stream=stream)
     fused = {}
     peak, _ = load_peaks()
@@ -393,7 +394,9 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
         Qm, Rm = np.linalg.qr(Z)
         U = Qm * (np.diag(Rm) / np.abs(np.diag(Rm)))
         row = {}
-        legs = [(list(range(k)), "mma_sync", "mma_sync"), (list(range(1, k + 1)), "cuda_cores", "auto")]
+        spread = [3, 9, 17, 22, 29][:k]
+        legs = [(list(range(k)), "mma_sync", "mma_sync"), (spread, "cuda_cores", "cuda_cores"),
+                (spread, "tensor_any_qubits", "auto")]
         if k >= 3:
             legs.insert(0, (list(range(k)), "tcgen05", "auto"))
         for qs, key, engine in legs:

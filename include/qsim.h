@@ -161,7 +161,11 @@ qs_status apply_fused(qs_sim* sim, const int* qubits, int k, const double* U);
  *                        streaming) when 3 <= k <= 5, the qubits are
  *                        0..k-1 in any order and N >= 12; else the mma.sync
  *                        tensor-core kernel when 2 <= k, the qubits are
- *                        0..k-1 and N >= k+4; else the CUDA-core kernel.
+ *                        0..k-1 and N >= k+4; other qubit sets with
+ *                        2 <= k and N >= 12 are first moved to bits 0..k-1
+ *                        by permute_qubits (one sweep), the gate runs there
+ *                        on tensor cores, and the qubits are moved back (one
+ *                        sweep); everything else runs the CUDA-core kernel.
  *  QS_FUSED_CUDA_CORES : the CUDA-core kernel for every gate.
  *  QS_FUSED_MMA_SYNC   : as AUTO without the tcgen05 kernel.
  * The default is QS_FUSED_AUTO.  Unknown values give QS_EINVAL.  A wait

@@ -327,9 +327,9 @@ constexpr size_t smem_bytes() {
 
 bool fused_tc05_eligible(const qs_sim* s, const int* qubits, int k) {
   if (s->enc != QS_C64 || k < 3 || k > 5 || s->N < 12) return false;
-  int mask = 0;
-  for (int m = 0; m < k; ++m) mask |= 1 << qubits[m];
-  return mask == (1 << k) - 1;
+  uint64_t mask = 0;
+  for (int m = 0; m < k; ++m) mask |= 1ull << qubits[m];
+  return mask == (1ull << k) - 1;
 }
 
 qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U) {

@@ -79,12 +79,12 @@ __global__ void __launch_bounds__(STPB) k_serve_small(const SmallEntry* __restri
 // CAS on the device counter `head`, runs it with the state in shared memory,
 // writes the results (for a final chunk) and marks the ring slot done with
 // the item's number (release, system scope).
-struct WorkItem {
+struct __align__(128) WorkItem {   // one cache line per item, never shared
   float2* state;
   const BGate<float>* gates;
   double* res;                 // host-mapped: [norm, P1(0..N-1)] for a final chunk
   int N, g0, g1, fresh, final_;
-  int pad;
+  int pad[21];
 };
 struct QueueCtl {              // host-mapped
   unsigned long long tail;     // items published
@@ -119,14 +119,19 @@ __device__ __forceinline__ BGate<float> gate_cg(const BGate<float>* p) {
   memcpy(&g, w, sizeof g);
   return g;
 }
-__device__ __forceinline__ WorkItem item_cg(const WorkItem* p) {
-  static_assert(sizeof(WorkItem) % 16 == 0, "work item layout");
+// A work item lives in host memory the host rewrites: its words are read
+// with system-scope strong loads, which observe the host's latest writes (a
+// weak load may be served by a line an earlier read left in the GPU's
+// caches).  The first 48 bytes hold the fields.
+__device__ __forceinline__ WorkItem item_sys(const WorkItem* p) {
+  static_assert(sizeof(WorkItem) == 128, "work item layout");
   WorkItem it;
-  const int4* q = (const int4*)p;
-  int4 w[sizeof(WorkItem) / 16];
+  unsigned long long w[6];
+  const unsigned long long* q = (const unsigned long long*)p;
 #pragma unroll
-  for (int i = 0; i < (int)(sizeof(WorkItem) / 16); ++i) w[i] = __ldcg(q + i);
-  memcpy(&it, w, sizeof it);
+  for (int i = 0; i < 6; ++i)
+    asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(w[i]) : "l"(q + i) : "memory");
+  memcpy(&it, w, sizeof w);
   return it;
 }
 
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(STPB) k_serve_persist(const WorkItem* ring, un
       }
       my = got;
       if (got >= 0) {
-        it = item_cg(ring + got % ring_n);
+        it = item_sys(ring + got % ring_n);
         atomicAdd(taken, 1ull);
       } else {
         atomicAdd(idle_exits, 1u);
@@ -330,8 +335,11 @@ extern "C" qs_status serve_run(qs_request* reqs, int n, const qs_serve_config* c
           o.nc = g.nc; o.c0 = g.controls[0]; o.c1 = g.controls[1]; o.t = g.target;
           for (int j = 0; j < 8; ++j) o.u[j] = (float)g.u[j];
         }
-        // pageable source: the copy completes before the call returns
-        if (cudaMemcpy(pool_base + a.goff, hg.data(), a.gbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        // on the stream of the small-state kernel, so the copy is ordered before
+        // the launch that reads it (a pageable cudaMemcpy may return before
+        // its DMA reaches the device)
+        if (cudaMemcpyAsync(pool_base + a.goff, hg.data(), a.gbytes, cudaMemcpyHostToDevice, streams[0]) !=
+            cudaSuccess) {
           qs_set_error("serve_run: gate upload failed");
           st = QS_ECUDA;
           break;
@@ -486,6 +494,8 @@ static qs_status serve_persistent(qs_request* reqs, int n, const qs_serve_config
   double* res_h = nullptr;
   unsigned long long* dcount = nullptr;   // head, taken
   unsigned int* didle = nullptr;
+  // streams[0]: the persistent kernel; 1..nstreams: larger states (and
+  // streams[nstreams] the gate uploads too)
   std::vector<cudaStream_t> streams(nstreams + 1, nullptr);
   cudaEvent_t kev = nullptr;
   std::vector<PActive> active;
@@ -510,6 +520,8 @@ static qs_status serve_persistent(qs_request* reqs, int n, const qs_serve_config
   double* res_d = nullptr;
   if (st == QS_OK) {
     memset(ctl_h, 0, sizeof(QueueCtl) + sizeof(unsigned long long) * (R - 1));
+    memset(ring_h, 0, sizeof(WorkItem) * R);
+    memset(res_h, 0, sizeof(double) * res_stride * R);
     cu(cudaHostGetDevicePointer((void**)&ring_d, ring_h, 0), "mapping");
     cu(cudaHostGetDevicePointer((void**)&ctl_d, ctl_h, 0), "mapping");
     cu(cudaHostGetDevicePointer((void**)&res_d, res_h, 0), "mapping");
@@ -579,7 +591,14 @@ static qs_status serve_persistent(qs_request* reqs, int n, const qs_serve_config
           o.nc = g.nc; o.c0 = g.controls[0]; o.c1 = g.controls[1]; o.t = g.target;
           for (int j = 0; j < 8; ++j) o.u[j] = (float)g.u[j];
         }
-        if (r.ngates) cu(cudaMemcpy(pool_base + a.goff, hg.data(), a.gbytes, cudaMemcpyHostToDevice), "gate upload");
+        // the copy must have reached device memory before the item is
+        // published: a pageable cudaMemcpy may return earlier, so copy on a
+        // stream of its own and wait for that stream
+        if (r.ngates) {
+          cu(cudaMemcpyAsync(pool_base + a.goff, hg.data(), a.gbytes, cudaMemcpyHostToDevice, streams[nstreams]),
+             "gate upload");
+          cu(cudaStreamSynchronize(streams[nstreams]), "gate upload");
+        }
         ++nsmall;
       } else {
         qs_status s2 = sim_create_in(r.N, QS_C64, pool_base + a.off, a.bytes, (void*)streams[a.stream], &a.sim);

@@ -186,3 +186,21 @@ def test_apply_fused_rejects(q):
         assert e.value.name == "QS_ENOTUNITARY"
         with pytest.raises(q.QSError):
             s.apply_fused([0, 0], np.eye(4))
+
+
+@pytest.mark.parametrize("N,qubits", [(14, [9, 2, 13]), (14, [0, 5, 1, 12]), (21, [3, 9, 17, 20, 11]),
+                                      (21, [4, 0, 2, 1, 3]), (16, [15, 7]), (22, [21, 0, 1, 2, 3])])
+def test_apply_fused_any_qubits_on_tensor_cores(q, N, qubits):
+    # complex64, "auto": qubits outside 0..k-1 are moved to the low bits,
+    # the tensor-core kernel runs there, and the qubits move back
+    g = np.random.default_rng(N + len(qubits))
+    v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
+    v0 /= np.linalg.norm(v0)
+    U = haar(1 << len(qubits), N)
+    with q.Sim(N, "c64") as s:
+        s.copy_in(v0)
+        s.apply_fused(qubits, U)
+        got = s.copy_out()
+    ref = v0.astype(np.complex64).astype(np.complex128)
+    sv.apply_dense(ref, N, qubits, U)
+    assert np.max(np.abs(got - ref)) <= 4e-5
