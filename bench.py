@@ -546,6 +546,35 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
                                "amplitude_terms_per_s": float(1 << P) * len(basis) / dt,
                                "max_abs_amplitude": float(np.max(np.abs(amps)))}
 
+    # batched small states (config 5's small end): 4096 states of N = 10, each
+    # with its own depth-5 layered circuit, in one launch after the autotuner
+    # (per-gate layouts, fusion width 1..4, states per CTA, CTA size) against
+    # the same circuits one state at a time through the per-gate sweeps
+    NB, SB = 10, 4096
+    circs = [wl.layered_circuit(NB, 5, seed=1000 + i) for i in range(SB)]
+    upd_b = sum(len(c) for c in circs) * float(1 << NB)
+    with qsim.Batch(NB, "c64", SB, stream=stream) as b:
+        b.set_circuits(circs)
+        b.run()
+        ms0, _ = _timed(torch, stream, lambda: b.run())
+        layout, threads, _ = b.autotune()
+        b.capture()
+        b.run()
+        ms1, _ = _timed(torch, stream, lambda: b.run())
+        fk, tb, th = b.tuning()
+    t0 = time.perf_counter()
+    for c in circs[:32]:
+        with qsim.Sim(NB, "c64", stream=stream) as s1:
+            s1.circuit_run(c, mode=0)
+            s1.sync()
+    per_state_s = (time.perf_counter() - t0) / 32
+    v["batched_small_states"] = {
+        "N": NB, "states": SB, "gates_per_state": len(circs[0]),
+        "default_ms": ms0, "tuned_graph_ms": ms1, "tuned": {"fuse_k": fk, "tile_bits": tb, "threads": th},
+        "value": upd_b / (ms1 / 1e3),
+        "per_gate_path_one_state_at_a_time_s": per_state_s * SB,
+        "per_gate_path_value": upd_b / (per_state_s * SB)}
+
     v["serving_stream"] = serving_variant(qsim, torch, stream, np, wl, full=False)
     torch.cuda.empty_cache()
     return v

@@ -129,6 +129,15 @@ qs_status sim_set_lazy_reset(qs_sim* sim, int on);
  * state). */
 qs_status sim_set_product_start(qs_sim* sim, int on);
 
+/* Arithmetic of the complex128 tile passes (circuit_run modes 1-3): on
+ * (nonzero, the default) each FP64 value is held as a double-float pair of
+ * FP32 numbers (about 48 significant bits; sums and products by error-free
+ * transformations) and computed on the FP32 pipes, which this GPU runs at 64
+ * times its FP64 rate; off: on the FP64 units.  Amplitudes stay FP64 in
+ * memory either way, and both agree with the FP64 oracle to 1e-12.  The
+ * paper's double-precision simulator (Sec. 4.1) computes in FP64. */
+qs_status sim_set_fp64_emulation(qs_sim* sim, int on);
+
 /* ---- gates (Sec. 2, Eq. (NUM2); Appendix A) ------------------------------ */
 /* Single-qubit gate: for every basis index i with bit `target` = 0,
  * (a_i, a_{i+2^target}) <- U (a_i, a_{i+2^target}) (Eq. (NUM2), Eq. (AQS0)).

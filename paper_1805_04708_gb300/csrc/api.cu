@@ -62,6 +62,7 @@ static qs_status init_handle(qs_sim* s, int N, qs_encoding enc, void* stream) {
   s->zero_pending = false;
   s->lazy_reset = false;
   s->product_start = true;
+  s->c128_df = true;
   QS_CUDA(cudaGetDevice(&s->device));
   QS_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
   if (enc == QS_ADAPT2) QS_CUDA(cudaMalloc(&s->a2dev, sizeof(A2Dev)));
@@ -188,6 +189,12 @@ extern "C" qs_status sim_set_lazy_reset(qs_sim* s, int on) {
 extern "C" qs_status sim_set_product_start(qs_sim* s, int on) {
   QS_TRY(check_sim(s));
   s->product_start = on != 0;
+  return QS_OK;
+}
+
+extern "C" qs_status sim_set_fp64_emulation(qs_sim* s, int on) {
+  QS_TRY(check_sim(s));
+  s->c128_df = on != 0;
   return QS_OK;
 }
 

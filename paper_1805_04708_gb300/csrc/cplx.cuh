@@ -5,6 +5,55 @@
 #include <cuda_runtime.h>
 #endif
 
+// ---------------------------------------------------------------------------
+// Double-float ("float-float") numbers: a value hi + lo held as two FP32
+// numbers with |lo| <= ulp(hi)/2, about 48 significant bits.  The sum and the
+// product follow the error-free transformations of Dekker (1971) and Knuth
+// (TAOCP vol. 2): TwoSum gives a + b = s + e exactly, TwoProd (one FMA)
+// a * b = p + e exactly, and a renormalisation keeps lo small.  Written with
+// the _rn intrinsics so that no multiply-add contraction changes them.  The
+// complex128 tile passes compute on these, on the FP32 pipes, instead of the
+// FP64 units (1/64 of the FP32 rate on this GPU).
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+  DF() = default;
+  __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ DF(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+  __device__ __forceinline__ DF(int i) : hi((float)i), lo(0.f) {}
+};
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ DF df_quick(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+  DF s = df_two_sum(a.hi, b.hi);
+  const DF t = df_two_sum(a.lo, b.lo);
+  s = df_quick(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_quick(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick(p, e);
+}
+__device__ __forceinline__ DF fma(DF a, DF b, DF c) { return a * b + c; }
+__device__ __forceinline__ bool operator!=(DF a, DF b) { return a.hi != b.hi || a.lo != b.lo; }
+
 template <typename R> struct __align__(2 * sizeof(R)) Cx { R x, y; };
 
 template <typename R>
@@ -34,6 +83,13 @@ __device__ __forceinline__ Cx<R> cmac2(Cx<R> u0, Cx<R> a0, Cx<R> u1, Cx<R> a1) {
   im = fma(u1.x, a1.y, im);
   im = fma(u1.y, a1.x, im);
   return cx<R>(re, im);
+}
+
+// complex128 amplitudes in memory are FP64 pairs; R = double computes on the
+// FP64 units, R = DF on FP32 pairs
+template <typename R> __device__ __forceinline__ Cx<R> from_mem(double2 x) { return cx<R>(R(x.x), R(x.y)); }
+template <typename R> __device__ __forceinline__ double2 to_mem(Cx<R> a) {
+  return make_double2(to_double(a.x), to_double(a.y));
 }
 
 // Storage <-> Cx conversions.

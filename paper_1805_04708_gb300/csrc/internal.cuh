@@ -31,6 +31,8 @@ struct qs_sim {
                       // them first
   bool product_start; // complex64 tile runs from a pending |0..0> start from
                       // the product state of their leading single-qubit gates
+  bool c128_df;       // complex128 tile passes compute in double-float (FP32
+                      // pairs) instead of on the FP64 units
 };
 // Write a pending |0..0> (no-op otherwise).
 qs_status materialize_state(qs_sim* s);

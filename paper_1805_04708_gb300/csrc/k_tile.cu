@@ -698,8 +698,13 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
   const unsigned grid = (unsigned)(ntiles < gmax ? ntiles : gmax);
   if (s->enc == QS_C128) {
     const size_t smem = ((size_t)16 << P.b) + tile_smem_header(4);
-    QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
+    if (s->c128_df) {   // double-float arithmetic on the FP32 pipes
+      QS_CUDA(cudaFuncSetAttribute(k_tile2<DF, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tile2<DF, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
+    } else {
+      QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
+    }
   } else if (cand > 0) {
     const size_t smem = ((size_t)8 << P.b) + tile_smem_header(5);
     QS_TRY(tile_jit_launch(s, P, kTileCandSync[cand], grid, smem));

@@ -96,6 +96,7 @@ __device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
 template <typename R> __device__ __forceinline__ Cx<R> ucx(const TOp& o, int k);
 template <> __device__ __forceinline__ Cx<float> ucx<float>(const TOp& o, int k) { return cx<float>(o.uf[2 * k], o.uf[2 * k + 1]); }
 template <> __device__ __forceinline__ Cx<double> ucx<double>(const TOp& o, int k) { return cx<double>(o.ud[2 * k], o.ud[2 * k + 1]); }
+template <> __device__ __forceinline__ Cx<DF> ucx<DF>(const TOp& o, int k) { return cx<DF>(DF(o.ud[2 * k]), DF(o.ud[2 * k + 1])); }
 
 // local index of register j under map m, given the thread part tl
 template <int RB>
@@ -198,6 +199,9 @@ template <typename R> __device__ __forceinline__ R uscal(const TOp& o) {
 template <typename R> __device__ __forceinline__ R shx(R x, int m);
 template <> __device__ __forceinline__ float shx<float>(float x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
 template <> __device__ __forceinline__ double shx<double>(double x, int m) { return __shfl_xor_sync(0xffffffffu, x, m); }
+template <> __device__ __forceinline__ DF shx<DF>(DF x, int m) {
+  return DF(__shfl_xor_sync(0xffffffffu, x.hi, m), __shfl_xor_sync(0xffffffffu, x.lo, m));
+}
 
 // lane-bit op: partner values by shuffle, each lane keeps its own output
 // CT: the op's structure is a compile-time constant (compiled passes), which
@@ -312,8 +316,8 @@ __device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
       const uint64_t g = base + woff + roff[jj];
       double2 x = s2[g], y = s2[g + 1];
-      v[2 * jj] = cx<double>(x.x, x.y);
-      v[2 * jj + 1] = cx<double>(y.x, y.y);
+      v[2 * jj] = from_mem<R>(x);
+      v[2 * jj + 1] = from_mem<R>(y);
     }
   }
 }
@@ -330,8 +334,8 @@ __device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t bas
 #pragma unroll
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj) {
       const uint64_t g = base + woff + roff[jj];
-      s2[g] = make_double2(v[2 * jj].x, v[2 * jj].y);
-      s2[g + 1] = make_double2(v[2 * jj + 1].x, v[2 * jj + 1].y);
+      s2[g] = to_mem<R>(v[2 * jj]);
+      s2[g + 1] = to_mem<R>(v[2 * jj + 1]);
     }
   }
 }
@@ -395,9 +399,9 @@ __device__ __forceinline__ void unstage_tile(const Cx<R>* st, Cx<R>* v, const ui
       const float4 x = ((const float4*)st)[l >> 1];
       v[2 * jj] = cx<float>(x.x, x.y);
       v[2 * jj + 1] = cx<float>(x.z, x.w);
-    } else {
-      v[2 * jj] = st[l];
-      v[2 * jj + 1] = st[l + 1];
+    } else {   // the stage holds the FP64 pairs as they were in memory
+      v[2 * jj] = from_mem<R>(((const double2*)st)[l]);
+      v[2 * jj + 1] = from_mem<R>(((const double2*)st)[l + 1]);
     }
   }
 }
@@ -599,8 +603,8 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
               const uint64_t w = P.tab[st.a][j];
               f = cx<R>(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)));
             } else {
-              f = cx<R>(__longlong_as_double((long long)P.tab[st.a][2 * j]),
-                        __longlong_as_double((long long)P.tab[st.a][2 * j + 1]));
+              f = cx<R>(R(__longlong_as_double((long long)P.tab[st.a][2 * j])),
+                        R(__longlong_as_double((long long)P.tab[st.a][2 * j + 1])));
             }
             v[j] = cmul_code(v[j], f, 4);
           }

@@ -78,6 +78,7 @@ _SIGS = {
     "sim_reset": (_I, [_P]),
     "sim_set_lazy_reset": (_I, [_P, _I]),
     "sim_set_product_start": (_I, [_P, _I]),
+    "sim_set_fp64_emulation": (_I, [_P, _I]),
     "apply_gate": (_I, [_P, _I, _D]),
     "apply_controlled": (_I, [_P, _IP, _I, _I, _D]),
     "apply_fused": (_I, [_P, _IP, _I, _D]),
@@ -439,6 +440,10 @@ class Sim:
         """Product start of complex64 tile runs from a pending |0..0> (see
         sim_set_product_start); on by default."""
         _check(_lib.sim_set_product_start(self._h, 1 if on else 0))
+
+    def set_fp64_emulation(self, on=True):
+        """complex128 tile passes in double-float (on, default) or FP64 (off)."""
+        _check(_lib.sim_set_fp64_emulation(self._h, 1 if on else 0))
 
     def apply_permutation(self, controls, reg_lo, reg_w, table):
         c, nc = _ints(controls)

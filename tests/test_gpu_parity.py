@@ -264,3 +264,20 @@ def test_shor_config_n30(q, enc):
     ks = np.argsort(P)[::-1][:8]
     periods = {shor.period_from_sample(int(k), X, G) for k in ks if k}
     assert any(p and r % p == 0 for p in periods)
+
+
+@pytest.mark.parametrize("df", [True, False])
+@pytest.mark.parametrize("N,kind", [(9, "mixed"), (14, "mixed"), (17, "layered"), (20, "gates")])
+def test_c128_tile_passes_fp64_and_double_float(q, df, N, kind):
+    # complex128 tile passes computed on FP32 pairs (double-float, the
+    # default) and on the FP64 units: both within 1e-12 of the oracle
+    recs = {"mixed": wl.random_mixed_circuit(N, 120, seed=300 + N),
+            "layered": wl.layered_circuit(N, 4, seed=N),
+            "gates": wl.random_gate_circuit(N, 150, seed=N)}[kind]
+    v0 = rand_state(N, 500 + N)
+    ref = circuit.run(v0.copy(), N, recs)
+    with q.Sim(N, "c128") as s:
+        s.set_fp64_emulation(df)
+        s.copy_in(v0)
+        s.circuit_run(recs, mode=1)
+        assert maxerr(s.copy_out(), ref) <= 1e-12
