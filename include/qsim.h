@@ -81,6 +81,16 @@ const char* qs_version(void);
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t qs_kernel_launches(void);
 
+/* Limit, process-wide, of the pipeline waits inside the tensor-core fused
+ * gate and the complex64 BEGIN MEASUREMENT kernels (waits for a tensor load,
+ * a conversion, an MMA or a free buffer): about `us` microseconds (0: give up
+ * at the first test; -1: the default, about one second).  A wait that runs
+ * out ends the kernel cleanly (the copies in flight are waited for with the
+ * full limit, the tensor memory is freed) and the call returns QS_ETIMEOUT;
+ * the next call with a normal limit runs as usual.  For tests of those exit
+ * paths; the paper has no counterpart. */
+qs_status qs_set_pipeline_wait_limit(int64_t us);
+
 /* ---- lifetime (QUBITS N, Appendix A; |0..0> of Eq. (appa0)) -------------- */
 /* Create an N-qubit state |0...0> (a_0 = 1, every other amplitude 0) in
  * encoding `enc`, in device memory the handle allocates and owns.

@@ -192,6 +192,15 @@ extern "C" qs_status sim_set_product_start(qs_sim* s, int on) {
   return QS_OK;
 }
 
+static std::atomic<uint32_t> g_pipe_spins{1u << 20};
+uint32_t pipeline_wait_spins(void) { return g_pipe_spins.load(); }
+
+extern "C" qs_status qs_set_pipeline_wait_limit(int64_t us) {
+  CHECK_ARG(us >= -1, "qs_set_pipeline_wait_limit: us = %lld", (long long)us);
+  g_pipe_spins.store(us < 0 ? (1u << 20) : (uint32_t)(us > (1ll << 30) ? (1ll << 30) : us));
+  return QS_OK;
+}
+
 extern "C" qs_status sim_set_fp64_emulation(qs_sim* s, int on) {
   QS_TRY(check_sim(s));
   s->c128_df = on != 0;

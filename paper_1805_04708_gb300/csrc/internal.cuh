@@ -156,6 +156,11 @@ qs_status a2_norm(qs_sim* s, double* out);
 qs_status a2_shorbox(qs_sim* s, int nx, uint64_t G, uint64_t y);
 qs_status a2_reset(qs_sim* s);
 
+// Spin limit of the pipeline waits of the tensor-core fused gate and of
+// BEGIN MEASUREMENT (each spin suspends for at most about a microsecond); the
+// drain waits of their exit paths keep the full limit.
+uint32_t pipeline_wait_spins(void);
+
 // Fixed-order compensated sum of n device doubles into *out (device).
 qs_status sum_partials(qs_sim* s, const double* part, int n, double* out);
 

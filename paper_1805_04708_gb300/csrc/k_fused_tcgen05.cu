@@ -126,7 +126,7 @@ __device__ __forceinline__ int swz(int r, int j) {
 template <int KR>
 __global__ void __launch_bounds__(TPB, 1)
     k_fused_tc05(const __grid_constant__ CUtensorMap tmap, uint64_t nstages, const float* __restrict__ Bg,
-                 int* __restrict__ err) {
+                 int* __restrict__ err, uint32_t spins) {
   using G = Geo<KR>;
   constexpr uint32_t IDESC = idesc_tf32(KR, 128);
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(TPB, 1)
       uint32_t n_issued = 0;
       for (uint32_t i = 0; i < nloc; ++i) {
         const int b = i % NBH;
-        if (!mbar_wait_or_abort(EMPTY(b), ((i / NBH) & 1) ^ 1, abort_flag)) break;
+        if (!mbar_wait_or_abort(EMPTY(b), ((i / NBH) & 1) ^ 1, abort_flag, spins)) break;
         const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
         const uint32_t hi = sA + b * STAGE_BYTES;
         mbar_expect_tx(FULL(b), STAGE_BYTES);
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(TPB, 1)
       uint32_t n_commit = 0;
       for (uint32_t i = 0; i < nloc; ++i) {
         const int b = i % NBH, l = i % NBL, t = i & 1;
-        if (!mbar_wait_or_abort(CONV(l), (i / NBL) & 1, abort_flag)) break;
-        if (!mbar_wait_or_abort(TFREE(t), ((i >> 1) & 1) ^ 1, abort_flag)) break;
+        if (!mbar_wait_or_abort(CONV(l), (i / NBL) & 1, abort_flag, spins)) break;
+        if (!mbar_wait_or_abort(TFREE(t), ((i >> 1) & 1) ^ 1, abort_flag, spins)) break;
         tc_fence_after();
         const uint32_t ahi = sA + b * STAGE_BYTES, alo = sLo + l * STAGE_BYTES;
 #pragma unroll
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(TPB, 1)
     const int ct = tid - 64;
     for (uint32_t i = 0; i < nloc; ++i) {
       const int b = i % NBH, l = i % NBL;
-      bool ok = mbar_wait_or_abort(FULL(b), (i / NBH) & 1, abort_flag);
-      ok = ok && mbar_wait_or_abort(LOFREE(l), ((i / NBL) & 1) ^ 1, abort_flag);
+      bool ok = mbar_wait_or_abort(FULL(b), (i / NBH) & 1, abort_flag, spins);
+      ok = ok && mbar_wait_or_abort(LOFREE(l), ((i / NBL) & 1) ^ 1, abort_flag, spins);
       if (!__all_sync(0xffffffffu, ok)) break;
       unsigned char* hi = sm + (sA - sb) + b * STAGE_BYTES;
       unsigned char* lo = sm + (sLo - sb) + l * STAGE_BYTES;
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(TPB, 1)
     const bool leader = (warp == 6 && lane == 0);
     for (uint32_t i = 0; i < nloc; ++i) {
       const int b = i % NBH, t = i & 1;
-      const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NBH) & 1, abort_flag));
+      const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NBH) & 1, abort_flag, spins));
       if (!ok) break;
       tc_fence_after();
       uint32_t v[4][16];
@@ -365,7 +365,7 @@ qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U
   const float* Bd = (const float*)s->scratch;
   auto go = [&](auto kern, size_t smem) -> qs_status {
     QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, TPB, smem, s->stream>>>(map, nstages, Bd, err);
+    kern<<<grid, TPB, smem, s->stream>>>(map, nstages, Bd, err, pipeline_wait_spins());
     return QS_OK;
   };
   switch (k) {

@@ -542,7 +542,7 @@ template <bool FIRST, bool VC, bool NORM>
 __global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ CUtensorMap map,
                                                          const __grid_constant__ XParams P,
                                                          double* __restrict__ tile_tot, double* __restrict__ part,
-                                                         int* __restrict__ err) {
+                                                         int* __restrict__ err, uint32_t spins) {
   using namespace qs_tma;
   extern __shared__ unsigned char xraw[];
   const uint32_t raw_s = smem_u32(xraw);
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(ETPB, 1) k_expect_tma(const __grid_constant__ 
   for (; k < nmine; ++k) {
     const int st = (int)(k % XSTAGES);
     const float2* xt = (const float2*)(buf + st * XTILE_BYTES);
-    const bool got = mbar_wait_or_abort(smem_u32(&full[st]), (uint32_t)((k / XSTAGES) & 1), abort_flag);
+    const bool got = mbar_wait_or_abort(smem_u32(&full[st]), (uint32_t)((k / XSTAGES) & 1), abort_flag, spins);
 #pragma unroll
     for (int jj = 0; jj < 16; ++jj) {
       const float4 q = *(const float4*)&xt[pa ^ xv::phys(xv::reg_a(2 * jj))];
@@ -954,7 +954,8 @@ static qs_status expect_views_impl(qs_sim* s, double* qx, double* qy, double* qz
       QS_TRY(expect_tensor_map(s, ps[i], &map));
       auto go = [&](auto kern) -> qs_status {
         QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XTMA_SMEM));
-        kern<<<grid, ETPB, XTMA_SMEM, s->stream>>>(map, ps[i], sc + tt_off, sc + part_off[i], err);
+        kern<<<grid, ETPB, XTMA_SMEM, s->stream>>>(map, ps[i], sc + tt_off, sc + part_off[i], err,
+                                                   pipeline_wait_spins());
         return QS_OK;
       };
       const bool vc = i == np - 1;

@@ -60,8 +60,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // As mbar_wait, but also gives up when another role has raised the abort
 // flag; raises it itself when the time runs out.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < WAIT_SPINS; ++it) {
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                   uint32_t spins = WAIT_SPINS) {
+  for (uint32_t it = 0; it < spins; ++it) {
     if (mbar_try(bar, parity, 1000)) return true;
     if (*abort_flag) return false;
   }

@@ -71,6 +71,7 @@ _SIGS = {
     "qs_last_error_string": (ctypes.c_char_p, []),
     "qs_version": (ctypes.c_char_p, []),
     "qs_kernel_launches": (ctypes.c_uint64, []),
+    "qs_set_pipeline_wait_limit": (_I, [ctypes.c_int64]),
     "sim_create": (_I, [_I, _I, _P, ctypes.POINTER(_P)]),
     "sim_create_in": (_I, [_I, _I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "sim_destroy": (_I, [_P]),
@@ -164,6 +165,12 @@ def version():
 
 def lib_path():
     return LIB_PATH
+
+
+def set_pipeline_wait_limit(us):
+    """Limit (microseconds; -1 = default) of the pipeline waits of the
+    tensor-core fused gate and BEGIN MEASUREMENT (see include/qsim.h)."""
+    _check(_lib.qs_set_pipeline_wait_limit(int(us)))
 
 
 def kernel_launches():
