@@ -413,13 +413,17 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
     torch.cuda.empty_cache()
 
     s128 = qsim.Sim(N, "c128", stream=stream)
-    for mode, key in ((1, "c128_tile_passes"), (0, "c128_per_gate_sweeps")):
-        def run128(mode=mode):
-            s128.reset()
-            s128.circuit_run(gates, mode=mode)
-        run128()
-        ms, _ = _timed(torch, stream, run128)
-        v[key] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
+    for df, suffix in ((True, ""), (False, "_fp64_units")):
+        s128.set_fp64_emulation(df)
+        for mode, key in ((1, "c128_tile_passes"), (0, "c128_per_gate_sweeps")):
+            def run128(mode=mode):
+                s128.reset()
+                s128.circuit_run(gates, mode=mode)
+            run128()
+            ms, _ = _timed(torch, stream, run128)
+            v[key + suffix] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms,
+                               "arithmetic": "double-float on FP32 pipes" if df else "FP64 units"}
+    s128.set_fp64_emulation(True)
     s128.close()
     del s128
     torch.cuda.empty_cache()

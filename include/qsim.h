@@ -139,12 +139,13 @@ qs_status sim_set_lazy_reset(qs_sim* sim, int on);
  * state). */
 qs_status sim_set_product_start(qs_sim* sim, int on);
 
-/* Arithmetic of the complex128 tile passes (circuit_run modes 1-3): on
- * (nonzero, the default) each FP64 value is held as a double-float pair of
- * FP32 numbers (about 48 significant bits; sums and products by error-free
- * transformations) and computed on the FP32 pipes, which this GPU runs at 64
- * times its FP64 rate; off: on the FP64 units.  Amplitudes stay FP64 in
- * memory either way, and both agree with the FP64 oracle to 1e-12.  The
+/* Arithmetic of the complex128 gate kernels (apply_gate, apply_controlled,
+ * circuit_run in every mode): on (nonzero, the default) each FP64 value is
+ * held as a double-float pair of FP32 numbers (about 48 significant bits;
+ * sums and products by error-free transformations) and computed on the FP32
+ * pipes, which this GPU runs at 64 times its FP64 rate; off: on the FP64
+ * units.  Amplitudes stay FP64 in memory either way, and both agree with the
+ * FP64 oracle to 1e-12.  Reductions and the dense fused gate stay FP64.  The
  * paper's double-precision simulator (Sec. 4.1) computes in FP64. */
 qs_status sim_set_fp64_emulation(qs_sim* sim, int on);
 

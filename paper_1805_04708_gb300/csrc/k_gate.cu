@@ -32,10 +32,11 @@ __device__ __forceinline__ uint64_t expand(uint64_t g, const Geom& G) {
 }
 
 // --- element adapters: apply a pair functor to storage elements -------------
-template <typename Op> struct PairD2 {
+// complex128 storage; R = double on the FP64 units, R = DF on FP32 pairs
+template <typename Op, typename R = double> struct PairD2 {
   Op op;
   __device__ __forceinline__ void operator()(double2& x, double2& y) const {
-    Cx<double> a = ld(x), b = ld(y); op.pair(a, b); st(x, a); st(y, b);
+    Cx<R> a = from_mem<R>(x), b = from_mem<R>(y); op.pair(a, b); x = to_mem<R>(a); y = to_mem<R>(b);
   }
 };
 template <typename Op> struct PairF2 {
@@ -62,10 +63,10 @@ template <typename Op> struct InregF4 {  // one pair: (v.lo, v.hi)
     v = make_float4(a.x, a.y, b.x, b.y);
   }
 };
-template <typename Op> struct OneD2 {
+template <typename Op, typename R = double> struct OneD2 {
   Op op;
   __device__ __forceinline__ void operator()(double2& v) const {
-    Cx<double> a = ld(v); op.one(a); st(v, a);
+    Cx<R> a = from_mem<R>(v); op.one(a); v = to_mem<R>(a);
   }
 };
 template <typename Op> struct OneF2 {
@@ -180,7 +181,7 @@ qs_status dispatch(qs_sim* s, const int* controls, int nc, int t, const double* 
     ins[n++] = t;
     uint64_t set = cmask | (upper ? (1ull << t) : 0ull);
     if constexpr (sizeof(R) == 8) {
-      return run_one<double2>(s, N, ins, n, set, OneD2<OpMul<R>>{op});
+      return run_one<double2>(s, N, ins, n, set, OneD2<OpMul<R>, R>{op});
     } else {
       if (minc >= 1 && t >= 1) {
         for (int i = 0; i < n; ++i) ins[i] -= 1;
@@ -196,7 +197,7 @@ qs_status dispatch(qs_sim* s, const int* controls, int nc, int t, const double* 
     for (int i = 0; i < nc; ++i) ins[n++] = controls[i];
     if constexpr (sizeof(R) == 8) {
       ins[n++] = t;
-      return run_pair<double2>(s, N, ins, n, cmask, 1ull << t, PairD2<Op>{op});
+      return run_pair<double2>(s, N, ins, n, cmask, 1ull << t, PairD2<Op, R>{op});
     } else {
       if (minc >= 1 && t >= 1) {
         ins[n++] = t;
@@ -226,7 +227,7 @@ qs_status dispatch(qs_sim* s, const int* controls, int nc, int t, const double* 
 }  // namespace
 
 qs_status launch_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]) {
-  if (s->enc == QS_C128) return dispatch<double>(s, controls, nc, target, u);
+  if (s->enc == QS_C128) return s->c128_df ? dispatch<DF>(s, controls, nc, target, u) : dispatch<double>(s, controls, nc, target, u);
   if (s->enc == QS_C64) return dispatch<float>(s, controls, nc, target, u);
   return QS_EUNSUPPORTED;
 }

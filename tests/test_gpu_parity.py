@@ -266,9 +266,10 @@ def test_shor_config_n30(q, enc):
     assert any(p and r % p == 0 for p in periods)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("df", [True, False])
 @pytest.mark.parametrize("N,kind", [(9, "mixed"), (14, "mixed"), (17, "layered"), (20, "gates")])
-def test_c128_tile_passes_fp64_and_double_float(q, df, N, kind):
+def test_c128_tile_passes_fp64_and_double_float(q, df, N, kind, mode):
     # complex128 tile passes computed on FP32 pairs (double-float, the
     # default) and on the FP64 units: both within 1e-12 of the oracle
     recs = {"mixed": wl.random_mixed_circuit(N, 120, seed=300 + N),
@@ -279,5 +280,5 @@ def test_c128_tile_passes_fp64_and_double_float(q, df, N, kind):
     with q.Sim(N, "c128") as s:
         s.set_fp64_emulation(df)
         s.copy_in(v0)
-        s.circuit_run(recs, mode=1)
+        s.circuit_run(recs, mode=mode)
         assert maxerr(s.copy_out(), ref) <= 1e-12
