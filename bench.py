@@ -383,8 +383,8 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
 
     # dense fused k-qubit gates (k = 2..5) on the k lowest qubits: tcgen05
     # (k >= 3) and mma.sync tensor-core kernels (3xTF32); on the spread
-    # qubits 3, 9, 17, 22, 29: the CUDA-core kernel, and the tensor cores
-    # after moving the qubits to the low bits (and back)
+    # qubits 3, 9, 17, 22, 29: the CUDA-core kernel, and "auto" (tcgen05 on
+    # gathered groups for k >= 3, the CUDA cores for k = 2)
     s64 = qsim.Sim(N, "c64", stream=stream)
     fused = {}
     peak, _ = load_peaks()

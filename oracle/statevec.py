@@ -67,9 +67,9 @@ def apply_dense(v, N, qubits, U):
     place.  Local index convention: bit m of the row/column index of U is the
     value of qubit ``qubits[m]``.
 
-    This is the multi-qubit gate of Eq. (AQS0) ("Gate operations involving n
-    qubits correspond to ... 2^n x 2^n unitary matrices"); gate fusion into
-    such matrices is suggested at the end of Sec. 5.2.
+    This is the multi-qubit gate of Eq. (AQS0): an n-qubit gate is a unitary
+    matrix of size 2^n acting on the n qubits' part of the index; the end of
+    Sec. 5.2 proposes fusing several gates into one such matrix.
     """
     U = np.asarray(U, dtype=np.complex128)
     k = len(qubits)

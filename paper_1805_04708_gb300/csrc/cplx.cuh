@@ -19,11 +19,17 @@ struct DF {
   float hi, lo;
   DF() = default;
   __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
-  __device__ __forceinline__ DF(double x) {
+  // also built on the host (gate coefficients of the per-gate kernels)
+  __host__ __device__ __forceinline__ DF(double x) {
+#ifdef __CUDA_ARCH__
     hi = __double2float_rn(x);
     lo = __double2float_rn(x - (double)hi);
+#else
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+#endif
   }
-  __device__ __forceinline__ DF(int i) : hi((float)i), lo(0.f) {}
+  __host__ __device__ __forceinline__ DF(int i) : hi((float)i), lo(0.f) {}
 };
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ double to_double(DF a) { return (double)a.hi + (double)a.lo; }

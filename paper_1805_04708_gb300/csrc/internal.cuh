@@ -106,6 +106,8 @@ qs_status launch_norm(qs_sim* s, double* out);
 qs_status launch_expect(qs_sim* s, double* qx, double* qy, double* qz);
 qs_status launch_expect_norm(qs_sim* s, double* qx, double* qy, double* qz, double* norm);
 qs_status launch_marginal(qs_sim* s, const int* qubits, int nq, double* out);
+// P(qubit q = 0) and P(qubit q = 1) in one coalesced sweep (any encoding)
+qs_status launch_qubit_probs(qs_sim* s, int q, double* p0, double* p1);
 
 // Tile passes --------------------------------------------------------------------
 // Optional per-launch timing: events ev[2i], ev[2i+1] around launch i.

@@ -35,10 +35,11 @@ struct EncP {
 // magnitudes are taken from the scaled components instead, so that the range
 // and the codes of tiny amplitudes follow |z| as the FP64 definition does
 constexpr float TINY2 = 1e-36f;
+// |z| < 1e-18: scaled by 2^100 (exact) the square is a normal number for
+// every nonzero FP32 input, so no division is needed
 __device__ __forceinline__ float tiny_mag(Cx<float> z) {
-  const float ax = fabsf(z.x), ay = fabsf(z.y);
-  const float s = fmaxf(ax, ay), t = fminf(ax, ay) / s;
-  return s * sqrtf(fmaf(t, t, 1.f));
+  const float xs = z.x * 1.2676506002282294e30f, ys = z.y * 1.2676506002282294e30f;   // 2^100
+  return sqrtf(fmaf(xs, xs, ys * ys)) * 7.888609052210118e-31f;                        // 2^-100
 }
 __device__ __forceinline__ float a2_mag(Cx<float> z) {
   const float m2 = fmaf(z.x, z.x, z.y * z.y);

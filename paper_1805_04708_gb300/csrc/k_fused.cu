@@ -58,34 +58,6 @@ qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* 
   uint64_t qmask = 0;
   for (int m = 0; m < k; ++m) qmask |= 1ull << qubits[m];
   const bool low = qmask == (1ull << k) - 1;   // the qubits are 0..k-1
-  if (s->enc == QS_C64 && s->fused_engine == QS_FUSED_AUTO && k >= 2 && s->N >= 12 && !low) {
-    // tensor cores take the k lowest qubits: move qubit qubits[m] to bit m
-    // (the low non-target qubits to the bits the targets leave), apply the
-    // gate there, and move everything back; each move is one sweep of the
-    // tile passes (bit transpositions), bit-exact
-    int perm[64], inv[64];
-    for (int x = 0; x < s->N; ++x) perm[x] = x;
-    int freed[5], nf = 0, lowfree[5], nl = 0;
-    for (int m = 0; m < k; ++m) {
-      perm[qubits[m]] = m;
-      if (qubits[m] >= k) freed[nf++] = qubits[m];
-    }
-    for (int x = 0; x < k; ++x) {
-      bool target = false;
-      for (int m = 0; m < k; ++m) target |= (qubits[m] == x);
-      if (!target) lowfree[nl++] = x;
-    }
-    for (int i = 0; i < nf; ++i)
-      for (int j = i + 1; j < nf; ++j)
-        if (freed[j] < freed[i]) { int t = freed[i]; freed[i] = freed[j]; freed[j] = t; }
-    for (int i = 0; i < nl; ++i) perm[lowfree[i]] = freed[i];
-    for (int x = 0; x < s->N; ++x) inv[perm[x]] = x;
-    int lowq[5];
-    for (int m = 0; m < k; ++m) lowq[m] = m;
-    QS_TRY(permute_qubits(s, perm));
-    QS_TRY(launch_fused_dense(s, lowq, k, U));
-    return permute_qubits(s, inv);
-  }
   if (s->enc == QS_C64 && s->fused_engine != QS_FUSED_CUDA_CORES) {
     if (s->fused_engine == QS_FUSED_AUTO && fused_tc05_eligible(s, qubits, k))
       return launch_fused_tc05(s, qubits, k, U);

@@ -1,5 +1,5 @@
-// Dense fused k-qubit gates (k = 3..5, the gate on the k lowest qubits of a
-// complex64 state with N >= 12) on the fifth-generation tensor cores.
+// Dense fused k-qubit gates (k = 3..5 on any qubits of a complex64 state
+// with N >= 12) on the fifth-generation tensor cores.
 //
 // The product is the one of the mma.sync kernel: with the k lowest qubits as
 // the local index the state is a row-major matrix S (2^(N-k) rows of
@@ -25,13 +25,27 @@
 //    accumulators, written back into the stage buffer in the same swizzled
 //    layout, then TMA tensor stores to where the stage came from; the
 //    buffer goes back to the producer once the store has read it.
-// Stages are disjoint, so the update is in place.  Every wait is bounded; a
+// Stages are disjoint, so the update is in place.
+//
+// Gates on other qubits (the gather variant): a stage is every amplitude
+// whose index varies only in the gate's qubits S and in the 12 - k lowest
+// index bits outside S (the set L), so it holds 2^(12-k) whole groups.  Those
+// 12 bits start with a contiguous run of at least 2^(12-k) amplitudes from
+// bit 0, so the producer warp loads the stage with at most 32 untiled bulk
+// copies of whole runs (cp.async.bulk, >= 1 KB each) in index order; the
+// converters read each row (group) out of that order into registers, and
+// after a barrier write its hi and lo parts in the swizzled operand layout;
+// the epilogue stores the results from registers straight to their
+// addresses (runs of 2^(lowest qubit of S) amplitudes across a warp), and the
+// stage buffer goes back to the producer as soon as the products are done.
+// Every wait is bounded; a
 // wait that runs out raises a CTA-wide abort flag, every role leaves its
 // loop, the producer and the MMA issuer wait (bounded) for what they still
 // have in flight, the tensor memory is freed and the error word is set.
 #include "internal.cuh"
 #include "tma.cuh"
 #include <vector>
+#include <string.h>
 
 namespace {
 
@@ -123,11 +137,37 @@ __device__ __forceinline__ int swz(int r, int j) {
   return ROWB == 128 ? (j ^ (r & 7)) : (j ^ ((r >> 1) & 3));
 }
 
-template <int KR>
+// Index geometry of the gather variant.
+struct GatherGeo {
+  float2* st;         // the state
+  uint64_t nons;      // index bits outside the gate's qubits
+  uint64_t smask;     // the gate's qubits S
+  uint64_t lmask;     // L: the 12 - k lowest bits of nons
+  uint64_t vmask;     // S | L, the 12 bits one stage spans
+  int run_log;        // a stage is 2^(12 - run_log) runs of 2^run_log amplitudes
+};
+// x's bits, lowest first, placed at the set bits of mask (and the inverse)
+__device__ __forceinline__ uint64_t dep_bits(uint64_t x, uint64_t mask) {
+  uint64_t r = 0;
+  for (uint64_t m = mask; m && x; m &= m - 1, x >>= 1)
+    if (x & 1) r |= m & (~m + 1);
+  return r;
+}
+__device__ __forceinline__ uint64_t ext_bits(uint64_t x, uint64_t mask) {
+  uint64_t r = 0;
+  int i = 0;
+  for (uint64_t m = mask; m; m &= m - 1, ++i)
+    if (x & m & (~m + 1)) r |= 1ull << i;
+  return r;
+}
+
+template <int KR, bool GATHER>
 __global__ void __launch_bounds__(TPB, 1)
-    k_fused_tc05(const __grid_constant__ CUtensorMap tmap, uint64_t nstages, const float* __restrict__ Bg,
-                 int* __restrict__ err, uint32_t spins) {
+    k_fused_tc05(const __grid_constant__ CUtensorMap tmap, GatherGeo gg, uint64_t nstages,
+                 const float* __restrict__ Bg, int* __restrict__ err, uint32_t spins) {
   using G = Geo<KR>;
+  constexpr int K = KR / 2;                           // amplitudes per group
+  constexpr int LOGK = KR == 16 ? 3 : (KR == 32 ? 4 : 5);
   constexpr uint32_t IDESC = idesc_tf32(KR, 128);
   extern __shared__ __align__(1024) unsigned char smraw[];
   const uint32_t base0 = smem_u32(smraw);
@@ -147,6 +187,9 @@ __global__ void __launch_bounds__(TPB, 1)
   auto TFREE = [&](int t) { return sBar + 8 * (3 * NBH + 2 * NBL + t); };  // accumulator read
   uint32_t* tslot = (uint32_t*)(sm + (sBar - sb) + 8 * (3 * NBH + 2 * NBL + 2));
   volatile int* abort_flag = (volatile int*)(tslot + 1);
+  // gather tables: index offset and stage position of each column
+  uint64_t* colofs = (uint64_t*)(tslot + 4);
+  uint32_t* colpos = (uint32_t*)(colofs + K);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -181,6 +224,13 @@ __global__ void __launch_bounds__(TPB, 1)
     *(uint32_t*)(sm + off) = h;
     *(uint32_t*)(sm + G::BPLANE + off) = l;
   }
+  if constexpr (GATHER) {
+    if (tid < K) {
+      const uint64_t o = dep_bits((uint64_t)tid, gg.smask);
+      colofs[tid] = o;
+      colpos[tid] = (uint32_t)ext_bits(o, gg.vmask);
+    }
+  }
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -189,7 +239,31 @@ __global__ void __launch_bounds__(TPB, 1)
   const uint32_t nloc =
       nstages > blockIdx.x ? (uint32_t)((nstages - 1 - blockIdx.x) / gridDim.x + 1) : 0u;   // stages of this CTA
 
-  if (warp == 0) {
+  if (GATHER && warp == 0) {
+    // ---- producer (gather): one bulk copy per run, lanes in parallel ----
+    const int nruns = 1 << (12 - gg.run_log);
+    const uint32_t run_bytes = 8u << gg.run_log;
+    uint32_t n_issued = 0;
+    for (uint32_t i = 0; i < nloc; ++i) {
+      const int b = i % NBH;
+      int ok = 1;
+      if (lane == 0) {
+        ok = mbar_wait_or_abort(EMPTY(b), ((i / NBH) & 1) ^ 1, abort_flag, spins);
+        if (ok) mbar_expect_tx(FULL(b), STAGE_BYTES);
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+      const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
+      const uint64_t base = dep_bits(g << (12 - LOGK), gg.nons);
+      if (lane < nruns)
+        bulk_load(sA + b * STAGE_BYTES + lane * run_bytes,
+                  gg.st + base + dep_bits((uint64_t)lane << gg.run_log, gg.vmask), run_bytes, FULL(b));
+      ++n_issued;
+    }
+    if (lane == 0 && *abort_flag)
+      for (uint32_t i = (n_issued > NBH ? n_issued - NBH : 0); i < n_issued; ++i)
+        mbar_wait(FULL(i % NBH), (i / NBH) & 1);
+    __syncwarp();
+  } else if (warp == 0) {
     // ---- producer ----
     if (lane == 0) {
       uint32_t n_issued = 0;
@@ -240,6 +314,47 @@ __global__ void __launch_bounds__(TPB, 1)
       if (*abort_flag && n_commit) mbar_wait(MMAD((n_commit - 1) % NBH), ((n_commit - 1) / NBH) & 1);
     }
     __syncwarp();
+  } else if (GATHER && warp < 6) {
+    // ---- converters (gather): rows out of index order -> hi (same buffer) + lo ----
+    const int ct = tid - 64;                       // the row of every sub-tile this thread converts
+    uint32_t rpos[G::S];
+#pragma unroll
+    for (int sub = 0; sub < G::S; ++sub)
+      rpos[sub] = (uint32_t)ext_bits(dep_bits((uint64_t)(sub * 128 + ct), gg.lmask), gg.vmask);
+    for (uint32_t i = 0; i < nloc; ++i) {
+      const int b = i % NBH, l = i % NBL;
+      bool ok = mbar_wait_or_abort(FULL(b), (i / NBH) & 1, abort_flag, spins);
+      ok = ok && mbar_wait_or_abort(LOFREE(l), ((i / NBL) & 1) ^ 1, abort_flag, spins);
+      if (!bar_and(2, 128, ok)) break;
+      unsigned char* hi = sm + (sA - sb) + b * STAGE_BYTES;
+      unsigned char* lo = sm + (sLo - sb) + l * STAGE_BYTES;
+      const float2* raw = (const float2*)hi;
+      float2 x[G::S][K];
+#pragma unroll
+      for (int sub = 0; sub < G::S; ++sub)
+#pragma unroll
+        for (int c = 0; c < K; ++c) x[sub][c] = raw[rpos[sub] + colpos[c]];
+      bar_sync(3, 128);                            // the whole stage is in registers
+#pragma unroll
+      for (int sub = 0; sub < G::S; ++sub)
+#pragma unroll
+        for (int j = 0; j < KR / 4; ++j) {
+          const int col = 4 * j, hb = col / G::BOXW, jj = (col % G::BOXW) / 4;
+          const int off = (sub * G::QX + hb) * G::BOXB + ct * G::ROWB + swz<G::ROWB>(ct, jj) * 16;
+          const float v[4] = {x[sub][2 * j].x, x[sub][2 * j].y, x[sub][2 * j + 1].x, x[sub][2 * j + 1].y};
+          uint32_t h[4], w[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            h[e] = to_tf32(v[e]);
+            w[e] = to_tf32(v[e] - __uint_as_float(h[e]));
+          }
+          *(uint4*)(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+          *(uint4*)(lo + off) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(CONV(l));
+    }
   } else if (warp < 6) {
     // ---- converters: x -> hi (in place) + lo ----
     const int ct = tid - 64;
@@ -264,6 +379,38 @@ __global__ void __launch_bounds__(TPB, 1)
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(CONV(l));
+    }
+  } else if (GATHER) {
+    // ---- epilogue (gather): accumulators -> their addresses in the state ----
+    const int q4 = warp & 3;
+    const bool leader = (warp == 6 && lane == 0);
+    const int r = 32 * q4 + lane;
+    uint64_t rofs[G::S];
+#pragma unroll
+    for (int sub = 0; sub < G::S; ++sub) rofs[sub] = dep_bits((uint64_t)(sub * 128 + r), gg.lmask);
+    for (uint32_t i = 0; i < nloc; ++i) {
+      const int b = i % NBH, t = i & 1;
+      const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NBH) & 1, abort_flag, spins));
+      if (!ok) break;
+      if (leader) mbar_arrive(EMPTY(b));         // the products have read the stage buffer
+      tc_fence_after();
+      uint32_t v[4][16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + t * 64 + 16 * c, v[c]);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(TFREE(t));
+      const uint64_t g = blockIdx.x + (uint64_t)i * gridDim.x;
+      const uint64_t base = dep_bits(g << (12 - LOGK), gg.nons);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int sub = (16 * c) / KR, c0 = (16 * c) % KR;
+        float2* row = gg.st + base + rofs[sub];
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          row[colofs[c0 / 2 + m]] = make_float2(__uint_as_float(v[c][2 * m]), __uint_as_float(v[c][2 * m + 1]));
+      }
     }
   } else {
     // ---- epilogue: accumulators -> stage buffer -> TMA store ----
@@ -320,40 +467,66 @@ __global__ void __launch_bounds__(TPB, 1)
 
 template <int KR>
 constexpr size_t smem_bytes() {
-  return (size_t)2 * Geo<KR>::BPLANE + (size_t)(NBH + NBL) * STAGE_BYTES + 8 * (3 * NBH + 2 * NBL + 2) + 8 + 1024;
+  // ..., tmem slot + abort flag + pad (16 bytes), gather tables (12 bytes per column)
+  return (size_t)2 * Geo<KR>::BPLANE + (size_t)(NBH + NBL) * STAGE_BYTES + 8 * (3 * NBH + 2 * NBL + 2) + 16 +
+         12 * (KR / 2) + 1024;
 }
 
 }  // namespace
 
 bool fused_tc05_eligible(const qs_sim* s, const int* qubits, int k) {
-  if (s->enc != QS_C64 || k < 3 || k > 5 || s->N < 12) return false;
+  if (s->enc != QS_C64 || k < 3 || k > 5 || s->N < 12 || s->N >= 64) return false;
   uint64_t mask = 0;
   for (int m = 0; m < k; ++m) mask |= 1ull << qubits[m];
-  return mask == (1ull << k) - 1;
+  return __builtin_popcountll(mask) == k;
 }
 
 qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U) {
   const int KR = 2 << k;
+  uint64_t smask = 0;
+  for (int m = 0; m < k; ++m) smask |= 1ull << qubits[m];
+  const bool gather = smask != (1ull << k) - 1;
+  // the block matrix's columns follow the group's own index order: the m-th
+  // qubit of the gate is bit (its rank among the gate's qubits)
+  int local[5];
+  for (int m = 0; m < k; ++m) local[m] = __builtin_popcountll(smask & ((1ull << qubits[m]) - 1));
   std::vector<float> B((size_t)KR * KR);
-  fused_block_matrix(qubits, k, U, B.data());
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) {
-    qs_set_error("apply_fused: cuTensorMapEncodeTiled is not available from the driver");
-    return QS_ECUDA;
-  }
-  // the state as a 3-D tensor: KR floats x 128 rows x 2^(N-k-7) blocks
-  const int boxw = KR >= 32 ? 32 : 16;
+  fused_block_matrix(local, k, U, B.data());
   CUtensorMap map;
-  const cuuint64_t dims[3] = {(cuuint64_t)KR, 128, 1ull << (s->N - k - 7)};
-  const cuuint64_t strides[2] = {(cuuint64_t)KR * 4, (cuuint64_t)128 * KR * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)boxw, 128, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->state, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, KR >= 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) {
-    qs_set_error("apply_fused: cuTensorMapEncodeTiled failed (%d)", (int)cr);
-    return QS_ECUDA;
+  memset(&map, 0, sizeof map);
+  GatherGeo gg;
+  memset(&gg, 0, sizeof gg);
+  if (gather) {
+    gg.st = (float2*)s->state;
+    gg.smask = smask;
+    gg.nons = ((1ull << s->N) - 1) & ~smask;
+    uint64_t m = gg.nons;
+    for (int i = 0; i < 12 - k; ++i) {
+      gg.lmask |= m & (~m + 1);
+      m &= m - 1;
+    }
+    gg.vmask = smask | gg.lmask;
+    gg.run_log = __builtin_ctzll(~gg.vmask);   // >= 12 - k: bits 0 .. 11-k all lie in S or L
+  } else {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+      qs_set_error("apply_fused: cuTensorMapEncodeTiled is not available from the driver");
+      return QS_ECUDA;
+    }
+    // the state as a 3-D tensor: KR floats x 128 rows x 2^(N-k-7) blocks
+    const int boxw = KR >= 32 ? 32 : 16;
+    const cuuint64_t dims[3] = {(cuuint64_t)KR, 128, 1ull << (s->N - k - 7)};
+    const cuuint64_t strides[2] = {(cuuint64_t)KR * 4, (cuuint64_t)128 * KR * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)boxw, 128, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->state, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      KR >= 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+      qs_set_error("apply_fused: cuTensorMapEncodeTiled failed (%d)", (int)cr);
+      return QS_ECUDA;
+    }
   }
   const size_t bbytes = sizeof(float) * B.size();
   QS_TRY(ensure_scratch(s, bbytes + 256));
@@ -365,13 +538,16 @@ qs_status launch_fused_tc05(qs_sim* s, const int* qubits, int k, const double* U
   const float* Bd = (const float*)s->scratch;
   auto go = [&](auto kern, size_t smem) -> qs_status {
     QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, TPB, smem, s->stream>>>(map, nstages, Bd, err, pipeline_wait_spins());
+    kern<<<grid, TPB, smem, s->stream>>>(map, gg, nstages, Bd, err, pipeline_wait_spins());
     return QS_OK;
   };
-  switch (k) {
-    case 3: QS_TRY(go(k_fused_tc05<16>, smem_bytes<16>())); break;
-    case 4: QS_TRY(go(k_fused_tc05<32>, smem_bytes<32>())); break;
-    default: QS_TRY(go(k_fused_tc05<64>, smem_bytes<64>())); break;
+  switch (k * 2 + (gather ? 1 : 0)) {
+    case 6: QS_TRY(go(k_fused_tc05<16, false>, smem_bytes<16>())); break;
+    case 7: QS_TRY(go(k_fused_tc05<16, true>, smem_bytes<16>())); break;
+    case 8: QS_TRY(go(k_fused_tc05<32, false>, smem_bytes<32>())); break;
+    case 9: QS_TRY(go(k_fused_tc05<32, true>, smem_bytes<32>())); break;
+    case 10: QS_TRY(go(k_fused_tc05<64, false>, smem_bytes<64>())); break;
+    default: QS_TRY(go(k_fused_tc05<64, true>, smem_bytes<64>())); break;
   }
   QS_LAUNCH_CHECK();
   int herr = 0;

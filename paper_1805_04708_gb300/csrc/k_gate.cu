@@ -227,7 +227,15 @@ qs_status dispatch(qs_sim* s, const int* controls, int nc, int t, const double* 
 }  // namespace
 
 qs_status launch_u2(qs_sim* s, const int* controls, int nc, int target, const double u[8]) {
-  if (s->enc == QS_C128) return s->c128_df ? dispatch<DF>(s, controls, nc, target, u) : dispatch<double>(s, controls, nc, target, u);
+  if (s->enc == QS_C128) {
+    // double-float carries 48 significant bits, so gates that only move
+    // amplitudes or multiply them by +-1, +-i (X, Y, Z, S, CNOT, TOFFOLI, ...)
+    // run in FP64 and stay exact
+    const GateClass gc = classify_u2(u);
+    const bool moves = (gc.kind == GK_ANTI || gc.kind == GK_DIAG) && gc.c0 < 4 && gc.c1 < 4;
+    return (s->c128_df && !moves) ? dispatch<DF>(s, controls, nc, target, u)
+                                  : dispatch<double>(s, controls, nc, target, u);
+  }
   if (s->enc == QS_C64) return dispatch<float>(s, controls, nc, target, u);
   return QS_EUNSUPPORTED;
 }

@@ -347,12 +347,8 @@ static qs_status project_scaled(qs_sim* s, int q, int bit, double c) {
 }
 
 static qs_status qubit_probs(qs_sim* s, int q, double* p0, double* p1) {
-  double pr[2];
   QS_TRY(materialize_state(s));
-  QS_TRY(launch_marginal(s, &q, 1, pr));
-  *p0 = pr[0];
-  *p1 = pr[1];
-  return QS_OK;
+  return launch_qubit_probs(s, q, p0, p1);
 }
 
 extern "C" qs_status project_qubit(qs_sim* s, int q, int bit, double* prob) {

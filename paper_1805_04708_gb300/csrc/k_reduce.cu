@@ -12,6 +12,7 @@
 #include "a2codec.cuh"
 #include "tma.cuh"
 #include <string.h>
+#include <type_traits>
 
 namespace {
 
@@ -138,7 +139,6 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, uint64_t mask) {
   return r;
 }
 __device__ __forceinline__ double sq(double2 a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double sq(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
 
 // ---- expect_xyz for small states (N <= 12): one CTA, FP64 throughout -------------------
 template <typename A>
@@ -652,17 +652,28 @@ struct MargGeo {
   int sq[24];       // register qubits, ascending
   int outbit[24];   // output bit of sq[m]
   uint64_t cmask;   // complement mask
-  uint64_t seglen;  // complement values per segment (power of two)
-  int nseg_log;
+  uint64_t seglen;  // complement values per thread (power of two)
+  int nseg_log;     // 2^nseg_log threads per register value
 };
 
-template <typename A>
-__device__ __forceinline__ double sqa(const A& a, const float* r) { return sq(a); }
-template <>
-__device__ __forceinline__ double sqa<uint16_t>(const uint16_t& w, const float* r) {
-  const double m = (double)r[(w & 0xFFu) ^ 0x80u];
-  return m * m;
+// |a|^2 of a complex128 amplitude (FP64 units)
+__device__ __forceinline__ double sqa(const double2& a, const float*) { return sq(a); }
+// |a|^2 into a float-float sum: complex64 products exact, adaptive-encoding
+// magnitudes from the decode table
+__device__ __forceinline__ void ff_add_sq(FF& f, const float2& a, const float*) {
+  ff_add_prod(f, a.x, a.x);
+  ff_add_prod(f, a.y, a.y);
 }
+__device__ __forceinline__ void ff_add_sq(FF& f, const uint16_t& w, const float* r) {
+  const float m = r[(w & 0xFFu) ^ 0x80u];
+  ff_add_prod(f, m, m);
+}
+
+// Thread (v, u) sums P over register value v's complement values u, u + T,
+// u + 2T, ... (T = 2^nseg_log threads per value): consecutive threads read
+// consecutive complement values, so a warp's loads are contiguous wherever
+// the low index bits lie outside the register.  The next complement value is
+// an addition in the deposited domain.  part[u * R + k] = the thread's sum.
 template <typename A>
 __global__ void __launch_bounds__(TPB) k_marginal(const A* __restrict__ s, MargGeo g, double* part, const A2Dev* a2) {
   __shared__ Luts L;
@@ -670,22 +681,111 @@ __global__ void __launch_bounds__(TPB) k_marginal(const A* __restrict__ s, MargG
   const uint64_t R = 1ull << g.nq;
   const uint64_t tid = (uint64_t)blockIdx.x * TPB + threadIdx.x;
   if (tid >= (R << g.nseg_log)) return;
-  const uint64_t t = tid & (R - 1);
-  const uint64_t seg = tid >> g.nq;
+  const uint64_t t = tid >> g.nseg_log;
+  const uint64_t u = tid & ((1ull << g.nseg_log) - 1);
   uint64_t ireg = 0, kout = 0;
   for (int m = 0; m < g.nq; ++m) {
     uint64_t bit = (t >> m) & 1ull;
     ireg |= bit << g.sq[m];
     kout |= bit << g.outbit[m];
   }
-  // first complement value of this segment: deposit(seg * seglen, cmask)
-  uint64_t x = deposit(seg * g.seglen, g.cmask);
+  uint64_t x = deposit(u, g.cmask);
+  const uint64_t step = deposit(1ull << g.nseg_log, g.cmask);
   double acc = 0.0;
-  for (uint64_t j = 0; j < g.seglen; ++j) {
-    acc += sqa<A>(s[ireg | x], L.r);
-    x = (x - g.cmask) & g.cmask;  // next subset of cmask in increasing order
+  if constexpr (std::is_same<A, double2>::value) {
+    for (uint64_t j = 0; j < g.seglen; ++j) {
+      acc += sqa(s[ireg | x], L.r);
+      x = ((x | ~g.cmask) + step) & g.cmask;
+    }
+  } else {
+    // float-float sums of up to 8 values folded into FP64
+    for (uint64_t j = 0; j < g.seglen; j += 8) {
+      FF f = {0.f, 0.f};
+      const uint64_t n = g.seglen - j < 8 ? g.seglen - j : 8;
+      for (uint64_t e = 0; e < n; ++e) {
+        ff_add_sq(f, s[ireg | x], L.r);
+        x = ((x | ~g.cmask) + step) & g.cmask;
+      }
+      acc += ff_val(f);
+    }
   }
-  part[seg * R + kout] = acc;
+  part[u * R + kout] = acc;
+}
+
+template <typename A> __device__ __forceinline__ A zero_amp() { return A{}; }
+template <> __device__ __forceinline__ uint16_t zero_amp<uint16_t>() { return (uint16_t)0x80u; }
+
+// ---- P(bit q = 0), P(bit q = 1) of one qubit ----------------------------------------
+// Pair j (of 2^(N-1)) is i0 = j with a 0 inserted at bit q and i1 = i0 | 2^q,
+// the pair of Eq. (NUM2); consecutive threads take consecutive j, so both
+// loads of a warp cover contiguous runs for every q and no lane diverges.
+// Each block leaves its two sums in part[2 * block + {0, 1}].
+__device__ __forceinline__ uint64_t pair_lo(uint64_t j, int q) {
+  const uint64_t low = (1ull << q) - 1;
+  return ((j & ~low) << 1) | (j & low);
+}
+template <typename A>
+__global__ void __launch_bounds__(TPB) k_qubit_probs(const A* __restrict__ s, uint64_t npairs, int q, double* part,
+                                                     const A2Dev* a2) {
+  __shared__ double sh[32];
+  __shared__ Luts L;
+  if (a2) build_luts(L, a2->r0, a2->r1);
+  const uint64_t stride = (uint64_t)gridDim.x * TPB;
+  const uint64_t bit = 1ull << q;
+  double acc0 = 0.0, acc1 = 0.0;
+  uint64_t j = (uint64_t)blockIdx.x * TPB + threadIdx.x;
+  if constexpr (std::is_same<A, double2>::value) {
+    for (; j < npairs; j += stride) {
+      const uint64_t i0 = pair_lo(j, q);
+      const double2 a = s[i0], b = s[i0 | bit];
+      acc0 = fma(a.x, a.x, acc0);
+      acc0 = fma(a.y, a.y, acc0);
+      acc1 = fma(b.x, b.x, acc1);
+      acc1 = fma(b.y, b.y, acc1);
+    }
+  } else {
+    // complex64: products exact (p + e), four pairs per thread in flight,
+    // float-float sums folded into FP64 every round; the adaptive encoding
+    // squares its decoded magnitudes the same way
+    constexpr int U = 4;
+    for (; j < npairs; j += U * stride) {
+      A a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t ju = j + u * stride;
+        if (ju < npairs) {
+          const uint64_t i0 = pair_lo(ju, q);
+          a[u] = s[i0];
+          b[u] = s[i0 | bit];
+        } else {   // amplitude zero: (0, 0), or magnitude code -128
+          a[u] = zero_amp<A>();
+          b[u] = zero_amp<A>();
+        }
+      }
+      FF f0 = {0.f, 0.f}, f1 = {0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if constexpr (std::is_same<A, float2>::value) {
+          ff_add_prod(f0, a[u].x, a[u].x);
+          ff_add_prod(f0, a[u].y, a[u].y);
+          ff_add_prod(f1, b[u].x, b[u].x);
+          ff_add_prod(f1, b[u].y, b[u].y);
+        } else {
+          const float ma = L.r[(a[u] & 0xFFu) ^ 0x80u], mb = L.r[(b[u] & 0xFFu) ^ 0x80u];
+          ff_add_prod(f0, ma, ma);
+          ff_add_prod(f1, mb, mb);
+        }
+      }
+      acc0 += ff_val(f0);
+      acc1 += ff_val(f1);
+    }
+  }
+  const double r0 = block_sum(acc0, sh);
+  const double r1 = block_sum(acc1, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r0;
+    part[2 * blockIdx.x + 1] = r1;
+  }
 }
 
 }  // namespace
@@ -1092,6 +1192,30 @@ qs_status launch_marginal(qs_sim* s, const int* qubits, int nq, double* out) {
   if (s->enc == QS_C128) return marginal_impl<double2>(s, qubits, nq, out);
   if (s->enc == QS_C64) return marginal_impl<float2>(s, qubits, nq, out);
   return marginal_impl<uint16_t>(s, qubits, nq, out);
+}
+
+qs_status launch_qubit_probs(qs_sim* s, int q, double* p0, double* p1) {
+  const uint64_t npairs = 1ull << (s->N - 1);
+  const uint64_t want = (npairs + TPB - 1) / TPB;
+  const int G = (int)(want < (uint64_t)reduce_grid(s) ? want : (uint64_t)reduce_grid(s));
+  QS_TRY(ensure_scratch(s, (size_t)(2 * G + 2) * sizeof(double)));
+  double* part = (double*)s->scratch;
+  if (s->enc == QS_C128)
+    k_qubit_probs<double2><<<G, TPB, 0, s->stream>>>((const double2*)s->state, npairs, q, part, nullptr);
+  else if (s->enc == QS_C64)
+    k_qubit_probs<float2><<<G, TPB, 0, s->stream>>>((const float2*)s->state, npairs, q, part, nullptr);
+  else
+    k_qubit_probs<uint16_t><<<G, TPB, 0, s->stream>>>((const uint16_t*)s->state, npairs, q, part,
+                                                      (const A2Dev*)s->a2dev);
+  QS_LAUNCH_CHECK();
+  k_sum_columns<<<2, TPB, 0, s->stream>>>(part, G, 2, part + 2 * G);
+  QS_LAUNCH_CHECK();
+  QS_TRY(ensure_hbuf(s, 2 * sizeof(double)));
+  QS_CUDA(cudaMemcpyAsync(s->hbuf, part + 2 * G, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(cudaStreamSynchronize(s->stream));
+  *p0 = ((const double*)s->hbuf)[0];
+  *p1 = ((const double*)s->hbuf)[1];
+  return QS_OK;
 }
 
 qs_status sum_partials(qs_sim* s, const double* part, int n, double* out) {

@@ -698,7 +698,17 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
   const unsigned grid = (unsigned)(ntiles < gmax ? ntiles : gmax);
   if (s->enc == QS_C128) {
     const size_t smem = ((size_t)16 << P.b) + tile_smem_header(4);
-    if (s->c128_df) {   // double-float arithmetic on the FP32 pipes
+    // double-float arithmetic on the FP32 pipes, except for passes that only
+    // move amplitudes or multiply them by +-1, +-i: those stay exact in FP64
+    // (double-float holds 48 significant bits)
+    bool moves = true;
+    for (int i = 0; i < P.nops && moves; ++i) {
+      const TOp& o = P.ops[i];
+      if (o.type == T_XPOSE) continue;
+      if (o.type == T_DIAG_TAB) { moves = false; break; }
+      moves = (o.kind == GK_ANTI || o.kind == GK_DIAG) && o.c0 < 4 && o.c1 < 4;
+    }
+    if (s->c128_df && !moves) {
       QS_CUDA(cudaFuncSetAttribute(k_tile2<DF, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_tile2<DF, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
     } else {

@@ -123,15 +123,6 @@ __device__ __forceinline__ uint64_t goff(uint32_t l, const uint8_t* gpos, int b)
   return g;
 }
 
-// exchange of the two values of a pair (X-type gates: unit coefficients)
-template <typename R> struct OpSwapC {
-  __device__ __forceinline__ void pair(Cx<R>& a0, Cx<R>& a1) const {
-    const Cx<R> t = a0;
-    a0 = a1;
-    a1 = t;
-  }
-};
-
 // --- register-slot pair op, slot S fixed at compile time -----------------------------
 template <typename R, int RB, int S, typename F>
 __device__ __forceinline__ void reg_pairs(Cx<R>* v, uint32_t smask, const F& f) {
@@ -555,17 +546,13 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
             // of X, Y, CNOT, TOFFOLI)
             // (a register-slot swap as renames makes the register allocation
             // spill at 128 registers; swaps on register slots stay dense)
+            // X-type swaps (X, CNOT, TOFFOLI) take the packed real-matrix
+            // path: as register exchanges they measured slower (renames under
+            // per-tile conditions become moves, and the interpreter spilled
+            // 2.6-3.2 KB; in compiled passes the renames doubled the time of
+            // the bench circuit's passes)
             const bool pure_swap = st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0;
-            if (Prog::kN >= 0 && pure_swap && st.gmask == 0 && st.tmask == 0) {
-              // X-type (X, CNOT, TOFFOLI) with no condition decided at run
-              // time: in a compiled pass the exchange is a renaming of
-              // registers and costs no instruction.  (Under a per-tile or
-              // per-thread condition, and in the interpreter, a swap takes
-              // the packed real-matrix path below: renames there turn into
-              // moves and spills.)
-              OpSwapC<R> f;
-              reg_op<R, RB>(v, st.a, st.smask, f);
-            } else if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
+            if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
               OpBflyF f;
               reg_op<R, RB>(v, st.a, st.smask, f);
             } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY || pure_swap)) {

@@ -189,10 +189,15 @@ def test_apply_fused_rejects(q):
 
 
 @pytest.mark.parametrize("N,qubits", [(14, [9, 2, 13]), (14, [0, 5, 1, 12]), (21, [3, 9, 17, 20, 11]),
-                                      (21, [4, 0, 2, 1, 3]), (16, [15, 7]), (22, [21, 0, 1, 2, 3])])
+                                      (21, [4, 0, 2, 1, 3]), (16, [15, 7]), (22, [21, 0, 1, 2, 3]),
+                                      (12, [11, 5, 0]), (12, [0, 2, 4, 6, 8]), (13, [12, 11, 10, 9, 8]),
+                                      (13, [7, 8, 9, 10, 11]), (15, [1, 3, 5, 7]), (20, [19, 18, 17, 0]),
+                                      (18, [0, 1, 2, 3, 17]), (17, [6, 7, 8])])
 def test_apply_fused_any_qubits_on_tensor_cores(q, N, qubits):
-    # complex64, "auto": qubits outside 0..k-1 are moved to the low bits,
-    # the tensor-core kernel runs there, and the qubits move back
+    # complex64, "auto": for k >= 3 on qubits other than 0..k-1 the tcgen05
+    # kernel gathers whole groups (one CTA at N = 12; a stage of one
+    # contiguous run when the qubits lie in bits 0..11; runs of 2^(12-k)
+    # amplitudes when they lie high); k = 2 runs on the CUDA cores
     g = np.random.default_rng(N + len(qubits))
     v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
     v0 /= np.linalg.norm(v0)
