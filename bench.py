@@ -334,6 +334,39 @@ def _timed(torch, stream, fn):
     return a.elapsed_time(b), r
 
 
+def per_gate_table(qsim, torch, stream, np, sim, N):
+    """One per-gate sweep (circuit_run mode 0) per gate class and target
+    t = 0..N-1, complex64: GB/s over the algorithmic bytes of the gate (a
+    dense or anti-diagonal gate reads and writes all 2^N amplitudes; a
+    one-sided diagonal and CNOT touch half of them, TOFFOLI a quarter) and
+    over the DRAM bytes the 32-byte sector floor forces: a sweep that skips
+    every other run of 2^t amplitudes still moves whole sectors when
+    2^t x 8 B < 32 B."""
+    SB = float(8 << N)
+    g = np.random.default_rng(5)
+    th = tuple(float(x) for x in g.uniform(0, 2 * np.pi, 3))
+    classes = (("U3", lambda t: [("U3", (t,), th)], 1.0),
+               ("X", lambda t: [("X", (t,), ())], 1.0),
+               ("T", lambda t: [("T", (t,), ())], 0.5),
+               ("CNOT", lambda t: [("CNOT", ((t + 7) % N, t), ())], 0.5),
+               ("TOFFOLI", lambda t: [("TOFFOLI", ((t + 7) % N, (t + 13) % N, t), ())], 0.25))
+    out = {"N": N, "unit": "GB/s", "peak_GB/s": load_peaks()[0]}
+    for name, recs, frac in classes:
+        rows = []
+        for t in range(N):
+            arr = qsim.gate_array(recs(t))
+            sim.circuit_run(arr, mode=0)
+            reps = 4
+            ms, _ = _timed(torch, stream, lambda: [sim.circuit_run(arr, mode=0) for _ in range(reps)])
+            ms /= reps
+            alg = 2.0 * SB * frac
+            moved = 2.0 * SB if (frac < 1.0 and (8 << t) < 32) else alg
+            rows.append({"t": t, "ms": round(ms, 4), "alg_GB/s": round(alg / (ms / 1e3) / 1e9, 1),
+                         "moved_GB/s": round(moved / (ms / 1e3) / 1e9, 1)})
+        out[name] = rows
+    return out
+
+
 def _order(y, G):
     r, f = 1, y % G
     while f != 1:
@@ -378,6 +411,7 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
         sim.circuit_run(gates, mode=0)
     ms, _ = _timed(torch, stream, per_gate_c64)
     v["c64_per_gate_sweeps"] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms}
+    v["c64_per_gate_by_target"] = per_gate_table(qsim, torch, stream, np, sim, N)
     sim.close()
     torch.cuda.empty_cache()
 
@@ -796,8 +830,8 @@ def run_profile_case(args):
       tile   : the random-gate circuit (N qubits, 200 gates, seed 1) through
                the tile passes twice (mode 2: after compiling and two runs
                per kernel candidate, four times), then <Qx,Qy,Qz> (complex64)
-      fused  : a dense k-qubit gate on qubits 0..k-1, applied three times
-               (complex64; the tcgen05 kernel for k >= 3)
+      fused  : a dense k-qubit gate on qubits 0..k-1 (or --fused-qubits),
+               applied three times (complex64; the tcgen05 kernel for k >= 3)
       adapt2 : one Haar U(2) on every qubit of the adaptive 2-byte state
                (the range and encode passes of each arithmetic gate)
       expect : BEGIN MEASUREMENT (<Qx,Qy,Qz> of every qubit) twice on the
@@ -861,8 +895,9 @@ def run_profile_case(args):
             Z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
             Qm, Rm = np.linalg.qr(Z)
             U = Qm * (np.diag(Rm) / np.abs(np.diag(Rm)))
+            qs = [int(x) for x in args.fused_qubits.split(",")] if args.fused_qubits else list(range(k))
             for _ in range(3):
-                s.apply_fused(list(range(k)), U)
+                s.apply_fused(qs, U)
         print("profile case %s N=%d norm %.12f" % (args.profile_case, N, s.norm()))
     torch.cuda.synchronize()
     return 0
@@ -883,6 +918,7 @@ def main(argv=None):
                     help="run a small workload for a profiler and exit")
     ap.add_argument("--qubits", type=int, default=26)
     ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--fused-qubits", default="", help="fused profile case: the gate's qubits (default 0..k-1)")
     ap.add_argument("--mode", type=int, default=1, help="circuit_run mode of the tile profile case")
     ap.add_argument("--tile-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="circuit_run mode of the timed step (0: 2 when NVRTC loads, else 1)")

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(TPB, 1)
   using G = Geo<KR>;
   constexpr int K = KR / 2;                           // amplitudes per group
   constexpr int LOGK = KR == 16 ? 3 : (KR == 32 ? 4 : 5);
+  constexpr int KH = K / 8;                           // column c = 8 a + m: tables per a and per m
   constexpr uint32_t IDESC = idesc_tf32(KR, 128);
   extern __shared__ __align__(1024) unsigned char smraw[];
   const uint32_t base0 = smem_u32(smraw);
@@ -187,9 +188,6 @@ __global__ void __launch_bounds__(TPB, 1)
   auto TFREE = [&](int t) { return sBar + 8 * (3 * NBH + 2 * NBL + t); };  // accumulator read
   uint32_t* tslot = (uint32_t*)(sm + (sBar - sb) + 8 * (3 * NBH + 2 * NBL + 2));
   volatile int* abort_flag = (volatile int*)(tslot + 1);
-  // gather tables: index offset and stage position of each column
-  uint64_t* colofs = (uint64_t*)(tslot + 4);
-  uint32_t* colpos = (uint32_t*)(colofs + K);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -223,13 +221,6 @@ __global__ void __launch_bounds__(TPB, 1)
     const int off = hb * (KR * G::ROWB) + n * G::ROWB + swz<G::ROWB>(n, kc >> 2) * 16 + (kc & 3) * 4;
     *(uint32_t*)(sm + off) = h;
     *(uint32_t*)(sm + G::BPLANE + off) = l;
-  }
-  if constexpr (GATHER) {
-    if (tid < K) {
-      const uint64_t o = dep_bits((uint64_t)tid, gg.smask);
-      colofs[tid] = o;
-      colpos[tid] = (uint32_t)ext_bits(o, gg.vmask);
-    }
   }
   fence_async_smem();
   tc_fence_before();
@@ -317,10 +308,16 @@ __global__ void __launch_bounds__(TPB, 1)
   } else if (GATHER && warp < 6) {
     // ---- converters (gather): rows out of index order -> hi (same buffer) + lo ----
     const int ct = tid - 64;                       // the row of every sub-tile this thread converts
-    uint32_t rpos[G::S];
+    // stage positions (bytes) of row ct of each sub-tile and of column
+    // c = 8 a + m (the parts add: they come from disjoint index bits)
+    uint32_t rpos[G::S], cph[KH], cpl[8];
 #pragma unroll
     for (int sub = 0; sub < G::S; ++sub)
-      rpos[sub] = (uint32_t)ext_bits(dep_bits((uint64_t)(sub * 128 + ct), gg.lmask), gg.vmask);
+      rpos[sub] = 8u * (uint32_t)ext_bits(dep_bits((uint64_t)(sub * 128 + ct), gg.lmask), gg.vmask);
+#pragma unroll
+    for (int a = 0; a < KH; ++a) cph[a] = 8u * (uint32_t)ext_bits(dep_bits((uint64_t)(8 * a), gg.smask), gg.vmask);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) cpl[m] = 8u * (uint32_t)ext_bits(dep_bits((uint64_t)m, gg.smask), gg.vmask);
     for (uint32_t i = 0; i < nloc; ++i) {
       const int b = i % NBH, l = i % NBL;
       bool ok = mbar_wait_or_abort(FULL(b), (i / NBH) & 1, abort_flag, spins);
@@ -328,12 +325,15 @@ __global__ void __launch_bounds__(TPB, 1)
       if (!bar_and(2, 128, ok)) break;
       unsigned char* hi = sm + (sA - sb) + b * STAGE_BYTES;
       unsigned char* lo = sm + (sLo - sb) + l * STAGE_BYTES;
-      const float2* raw = (const float2*)hi;
       float2 x[G::S][K];
 #pragma unroll
       for (int sub = 0; sub < G::S; ++sub)
 #pragma unroll
-        for (int c = 0; c < K; ++c) x[sub][c] = raw[rpos[sub] + colpos[c]];
+        for (int a = 0; a < KH; ++a) {
+          const unsigned char* rb = hi + rpos[sub] + cph[a];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) x[sub][8 * a + m] = *(const float2*)(rb + cpl[m]);
+        }
       bar_sync(3, 128);                            // the whole stage is in registers
 #pragma unroll
       for (int sub = 0; sub < G::S; ++sub)
@@ -385,9 +385,14 @@ __global__ void __launch_bounds__(TPB, 1)
     const int q4 = warp & 3;
     const bool leader = (warp == 6 && lane == 0);
     const int r = 32 * q4 + lane;
-    uint64_t rofs[G::S];
+    // index offsets of row r of each sub-tile and of column c = 8 a + m
+    uint64_t rofs[G::S], coh[KH], col[8];
 #pragma unroll
     for (int sub = 0; sub < G::S; ++sub) rofs[sub] = dep_bits((uint64_t)(sub * 128 + r), gg.lmask);
+#pragma unroll
+    for (int a = 0; a < KH; ++a) coh[a] = dep_bits((uint64_t)(8 * a), gg.smask);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) col[m] = dep_bits((uint64_t)m, gg.smask);
     for (uint32_t i = 0; i < nloc; ++i) {
       const int b = i % NBH, t = i & 1;
       const bool ok = bar_and(1, 128, mbar_wait_or_abort(MMAD(b), (i / NBH) & 1, abort_flag, spins));
@@ -405,11 +410,11 @@ __global__ void __launch_bounds__(TPB, 1)
       const uint64_t base = dep_bits(g << (12 - LOGK), gg.nons);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int sub = (16 * c) / KR, c0 = (16 * c) % KR;
-        float2* row = gg.st + base + rofs[sub];
+        const int sub = (16 * c) / KR, a = ((16 * c) % KR) / 16;   // columns 8 a .. 8 a + 7
+        float2* row = gg.st + (base + rofs[sub] + coh[a]);
 #pragma unroll
         for (int m = 0; m < 8; ++m)
-          row[colofs[c0 / 2 + m]] = make_float2(__uint_as_float(v[c][2 * m]), __uint_as_float(v[c][2 * m + 1]));
+          row[col[m]] = make_float2(__uint_as_float(v[c][2 * m]), __uint_as_float(v[c][2 * m + 1]));
       }
     }
   } else {
@@ -467,9 +472,7 @@ __global__ void __launch_bounds__(TPB, 1)
 
 template <int KR>
 constexpr size_t smem_bytes() {
-  // ..., tmem slot + abort flag + pad (16 bytes), gather tables (12 bytes per column)
-  return (size_t)2 * Geo<KR>::BPLANE + (size_t)(NBH + NBL) * STAGE_BYTES + 8 * (3 * NBH + 2 * NBL + 2) + 16 +
-         12 * (KR / 2) + 1024;
+  return (size_t)2 * Geo<KR>::BPLANE + (size_t)(NBH + NBL) * STAGE_BYTES + 8 * (3 * NBH + 2 * NBL + 2) + 8 + 1024;
 }
 
 }  // namespace
