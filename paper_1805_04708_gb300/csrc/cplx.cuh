@@ -183,6 +183,25 @@ struct OpBflyF {
     a1 = cx<float>(B1.x, B1.y);
   }
 };
+// The butterfly with the two amplitudes' roles possibly exchanged (a
+// relabelled index bit: a0 then holds the pair's upper element): s0 = (1, 1),
+// s1 = (-1, -1) give (a0 + a1, a0 - a1); s0 = (-1, -1), s1 = (1, 1) give
+// (a1 - a0, a1 + a0).
+struct OpBflyS {
+  float2 s0, s1;
+  __device__ __forceinline__ void pair(Cx<float>& a0, Cx<float>& a1) const {
+    const float2 A0 = make_float2(a0.x, a0.y), A1 = make_float2(a1.x, a1.y);
+#ifdef QS_HAVE_F32X2
+    const float2 B0 = __ffma2_rn(s0, A0, A1);
+    const float2 B1 = __ffma2_rn(s1, A1, A0);
+#else
+    const float2 B0 = make_float2(fmaf(s0.x, A0.x, A1.x), fmaf(s0.x, A0.y, A1.y));
+    const float2 B1 = make_float2(fmaf(s1.x, A1.x, A0.x), fmaf(s1.x, A1.y, A0.y));
+#endif
+    a0 = cx<float>(B0.x, B0.y);
+    a1 = cx<float>(B1.x, B1.y);
+  }
+};
 template <typename R> struct OpMul {
   Cx<R> f; int c;
   __device__ __forceinline__ void one(Cx<R>& a) const { a = cmul_code(a, f, c); }

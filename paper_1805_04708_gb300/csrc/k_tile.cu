@@ -114,6 +114,80 @@ static int rewrite_pass(const qs_gate* gates, const int* gidx, int ng, qs_gate* 
 // Build the op list of one pass.  tile: bitmask of the tile's global bits
 // (contains bits 0..5), gidx: the gates in order.  Returns false if the op
 // list overflows (caller splits the pass).
+// Relabelled swaps (complex64 passes).  A pure swap (X, CNOT, TOFFOLI) whose
+// controls lie outside the register slots and the lanes exchanges the two
+// halves of its target bit wherever the controls hold, and the same in every
+// lane of a warp: the pass then records the bit as relabelled (T_FLIP, a
+// per-thread XOR mask on the local index) instead of moving data.  Later ops
+// that meet a relabelled bit: an op on that register slot swaps the roles of
+// its pair (flag pad[1]; pad[2] holds the slot's local bit), lane ops and
+// conditions read the mask, a transpose writes every element to its own
+// place (and clears the mask), the store XORs the bits' global offset into
+// the address; an op that needs a register slot in place (a control on it, a
+// factor table) first exchanges it back (T_UNFLIP), and so does slot 0
+// (inside a 16-byte access) before a transpose and before the store.
+// Returns false when the inserted ops do not fit (the pass keeps its ops).
+static bool relabel_swaps(TileParams2* P, int nops, int RB, int* nops_out) {
+  static thread_local TOp out[MAX_TOPS];
+  int m = 0;
+  TMap cur = P->init;
+  int mi = 0;
+  uint32_t M = 0;                    // local bits that may be relabelled
+  const uint32_t lane_bits = 0x3Eu;  // local bits 1..5
+  bool any = false, fits = true;
+  auto gbit = [&](int lb) { return 1ull << (lb < LOW_BITS ? lb : P->gpos[lb]); };
+  auto push = [&](const TOp& o) {
+    if (m >= MAX_TOPS) { fits = false; return; }
+    out[m++] = o;
+  };
+  auto unflip = [&](int slot) {
+    TOp u;
+    memset(&u, 0, sizeof u);
+    u.type = T_UNFLIP;
+    u.a = (uint8_t)slot;
+    u.pad[2] = cur.reg[slot];
+    u.gtbit = gbit(cur.reg[slot]);
+    M &= ~(1u << cur.reg[slot]);
+    push(u);
+  };
+  for (int i = 0; i < nops && fits; ++i) {
+    TOp o = P->ops[i];
+    const bool swap = (o.type == T_REG || o.type == T_LANE) && o.kind == GK_ANTI && o.c0 == 0 && o.c1 == 0 &&
+                      o.smask == 0 && (o.tmask & lane_bits) == 0 && o.pad[0] == 0;
+    if (swap) {
+      const int lb = o.type == T_REG ? cur.reg[o.a] : o.a + 1;
+      o.type = T_FLIP;
+      o.a = (uint8_t)lb;
+      o.gtbit = gbit(lb);
+      M |= 1u << lb;
+      any = true;
+      push(o);
+      continue;
+    }
+    if (o.type == T_XPOSE) {
+      if (M & 1u) unflip(0);
+      push(o);
+      cur = P->maps[mi++];
+      M = 0;
+      continue;
+    }
+    for (int sl = 0; sl < RB; ++sl) {
+      const bool needed = (o.type == T_DIAG_TAB) || ((o.smask >> sl) & 1u);
+      if (needed && ((M >> cur.reg[sl]) & 1u)) unflip(sl);
+    }
+    if (o.type == T_REG || o.type == T_DIAG_REG) {
+      o.pad[2] = cur.reg[o.a];
+      if ((M >> cur.reg[o.a]) & 1u) o.pad[1] = 1;
+    }
+    push(o);
+  }
+  if (fits && (M & 1u)) unflip(0);
+  if (!fits || !any) return false;
+  for (int i = 0; i < m; ++i) P->ops[i] = out[i];
+  *nops_out = m;
+  return true;
+}
+
 static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, int N, int b, int RB, uint64_t tile,
                        TileParams2* P, bool real_kinds) {
   static thread_local qs_gate seq[MAX_TOPS * 2];
@@ -409,6 +483,7 @@ static bool build_pass(const qs_gate* gates_in, const int* gidx_in, int ng_in, i
     }
     i = (j > i) ? j : i + 1;
   }
+  if (real_kinds) relabel_swaps(P, nops, RB, &nops);
   P->nops = nops;
   P->fin = cur;
   P->last_xpose = -1;

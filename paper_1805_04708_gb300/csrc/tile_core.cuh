@@ -15,7 +15,13 @@
 //   the remaining 3 local bits              -> the 8 warps
 // A gate on a register bit or a lane bit runs without shared memory; a gate on
 // a warp bit first swaps that bit into a register slot by one shared-memory
-// transpose.  Diagonal gates run in place whatever their target (the target
+// transpose.  A pure swap (X, CNOT, TOFFOLI) whose controls lie outside the
+// register slots and the lanes moves no data: it relabels its target bit.
+// Each thread keeps the relabelled local bits in a mask xl (the element a
+// thread holds at physical local index p is the tile's element p ^ xl; xl is
+// the same in all lanes of a warp) and their global offset gx; conditions, the
+// roles of a pair, the transposes and the store address read them, and an op
+// that needs a register slot in place first exchanges it back (T_UNFLIP).  Diagonal gates run in place whatever their target (the target
 // bit is known for every element), and controls may be any bit (a control
 // outside the tile is a per-tile condition).  The host planner may take a
 // gate ahead of earlier gates left for later passes only when it commutes
@@ -42,17 +48,20 @@ constexpr int MAX_TOPS = 96;
 constexpr int LOW_BITS = 4;   // index bits always in the tile (16-amplitude runs)
 
 enum TOpType : uint8_t { T_REG = 0, T_LANE = 1, T_DIAG_REG = 2, T_DIAG_THR = 3, T_DIAG_OUT = 4, T_XPOSE = 5,
-                         T_DIAG_TAB = 6 };
+                         T_DIAG_TAB = 6, T_FLIP = 7, T_UNFLIP = 8 };
 constexpr int MAX_TABS = 8;   // per-register factor tables of a pass
 
 struct TOp {
   uint8_t type, kind, c0, c1;
-  uint8_t a;           // T_REG / T_DIAG_REG: register slot; T_LANE: lane bit; T_DIAG_THR: local bit
-  uint8_t pad[3];
+  uint8_t a;           // T_REG / T_DIAG_REG / T_UNFLIP: register slot; T_LANE: lane bit;
+                       // T_DIAG_THR / T_FLIP: local bit
+  uint8_t pad[3];      // [0]: fold flag of per-thread diagonals; [1]: the target
+                       // slot may be relabelled; [2]: local bit of the slot
   uint32_t smask;      // control bits among the register slots (bits of j)
   uint32_t tmask;      // control bits among lane / warp local bits (local-index mask)
   uint64_t gmask;      // control bits outside the tile
-  uint64_t gtbit;      // T_DIAG_OUT: the target bit (global)
+  uint64_t gtbit;      // T_DIAG_OUT: the target bit (global); T_FLIP / T_UNFLIP: the
+                       // global offset of the relabelled local bit
   float uf[8];
   double ud[8];
 };
@@ -199,9 +208,9 @@ template <> __device__ __forceinline__ DF shx<DF>(DF x, int m) {
 // enables the butterfly form of GK_BFLY; the interpreter runs GK_BFLY as the
 // real matrix [[1, 1], [1, -1]] that its coefficients hold.
 template <typename R, int RB, bool SWAP, bool CT, class OS>
-__device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, int lane, bool tok) {
+__device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, int lane, bool tok, uint32_t xl) {
   const int m = 1 << st.a;
-  const bool hi = (lane >> st.a) & 1;
+  const bool hi = ((lane >> st.a) ^ (xl >> (st.a + 1))) & 1;   // the tile's bit, not the lane's
   Cx<R> u00 = ucx<R>(o, 0), u01 = ucx<R>(o, 1), u10 = ucx<R>(o, 2), u11 = ucx<R>(o, 3);
   if constexpr (sizeof(R) == 4) {
     if (SWAP && st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0) {
@@ -312,14 +321,17 @@ __device__ __forceinline__ void load_tile(const void* s, Cx<R>* v, uint64_t base
     }
   }
 }
+// gx: the global offset of the relabelled local bits (never bit 0), XORed
+// into each element's offset inside the tile
 template <typename R, int RB>
 __device__ __forceinline__ void store_tile(void* s, const Cx<R>* v, uint64_t base, const uint64_t* roff, uint64_t woff,
-                                           int lane) {
+                                           uint64_t gx) {
   if constexpr (sizeof(R) == 4) {
     float4* s4 = (float4*)s;
 #pragma unroll
     for (int jj = 0; jj < (1 << (RB - 1)); ++jj)
-      s4[(base + woff + roff[jj]) >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
+      s4[(base + ((woff + roff[jj]) ^ gx)) >> 1] =
+          make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
   } else {
     double2* s2 = (double2*)s;
 #pragma unroll
@@ -477,6 +489,8 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
       stage_tile<R, RB>(s, stg, base_nxt, roff_in, woff_in, lreg_in, tl_in);
     TMap cur = P.init;
     uint32_t tl = thread_part(cur, lane, warp);
+    uint32_t xl = 0;   // relabelled local bits of this tile (the same in every lane of a warp)
+    uint64_t gx = 0;   // their global offset (for the store)
     Cx<R> fac = cx<R>((R)1, (R)0);
     int mapi = 0;
     const int nops = Prog::kN >= 0 ? Prog::kN : P.nops;
@@ -492,7 +506,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
         // write every register at its local index, read back under the new map
 #pragma unroll
         for (int jj = 0; jj < NR / 2; ++jj) {
-          const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
+          const uint32_t l = lidx<RB>(cur, 2 * jj, tl) ^ xl;   // the element's place in the tile
           if constexpr (sizeof(R) == 4) {
             ((float4*)xb)[l >> 1] = make_float4(v[2 * jj].x, v[2 * jj].y, v[2 * jj + 1].x, v[2 * jj + 1].y);
           } else {
@@ -503,6 +517,8 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
         __syncthreads();
         cur = P.maps[mapi++];
         tl = thread_part(cur, lane, warp);
+        xl = 0;
+        gx = 0;
 #pragma unroll
         for (int jj = 0; jj < NR / 2; ++jj) {
           const uint32_t l = lidx<RB>(cur, 2 * jj, tl);
@@ -521,11 +537,11 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
         continue;
       }
       const bool gok = (base & st.gmask) == st.gmask;       // outer controls
-      const bool tok = (tl & st.tmask) == st.tmask;         // lane / warp controls
+      const bool tok = ((tl ^ xl) & st.tmask) == st.tmask;  // lane / warp controls
       if (st.pad[0] != 0) {
         // folded run of per-thread diagonals: multiply the factor, apply at the end
         if (gok && tok) {
-          const bool one = (st.type == T_DIAG_THR) ? ((tl >> st.a) & 1) : ((base & st.gtbit) != 0);
+          const bool one = (st.type == T_DIAG_THR) ? (((tl ^ xl) >> st.a) & 1) : ((base & st.gtbit) != 0);
           if ((one ? st.c1 : st.c0) != 0) fac = cmul_code(fac, ucx<R>(o, one ? 3 : 0), 4);
         }
         if (st.pad[0] == 2) {
@@ -539,6 +555,32 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
       }
       if (!gok) continue;
       switch (st.type) {
+        case T_FLIP:   // gtbit: the global offset of local bit a
+          if (tok) {
+            xl ^= 1u << st.a;
+            gx ^= st.gtbit;
+          }
+          break;
+        case T_UNFLIP:
+          // the exchange as the real matrix [[0, 1], [1, 0]] (the code shape of
+          // the other real ops: plain register exchanges made the interpreter
+          // spill)
+          if ((xl >> st.pad[2]) & 1) {
+            if constexpr (sizeof(R) == 4) {
+              OpRealF f;
+              f.u00 = f.u11 = make_float2(0.f, 0.f);
+              f.u01 = f.u10 = make_float2(1.f, 1.f);
+              reg_op<R, RB>(v, st.a, 0u, f);
+            } else {
+              OpAnti<R> f;
+              f.f01 = f.f10 = cx<R>((R)1, (R)0);
+              f.c0 = f.c1 = 0;
+              reg_op<R, RB>(v, st.a, 0u, f);
+            }
+            xl ^= 1u << st.pad[2];
+            gx ^= st.gtbit;
+          }
+          break;
         case T_REG: {
           if (!tok) break;
           if constexpr (sizeof(R) == 4) {
@@ -551,17 +593,30 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
             // per-tile conditions become moves, and the interpreter spilled
             // 2.6-3.2 KB; in compiled passes the renames doubled the time of
             // the bench circuit's passes)
+            // (a relabelled target slot exchanges the roles of the pair's
+            // two amplitudes: the matrix is taken as X U X)
             const bool pure_swap = st.kind == GK_ANTI && st.c0 == 0 && st.c1 == 0;
+            const bool fl = st.pad[1] != 0 && ((xl >> st.pad[2]) & 1);
             if ((FEAT & FEAT_HAD) && Prog::kN >= 0 && st.kind == GK_BFLY) {
-              OpBflyF f;
-              reg_op<R, RB>(v, st.a, st.smask, f);
+              if (st.pad[1] != 0) {
+                OpBflyS f;
+                f.s0 = fl ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+                f.s1 = fl ? make_float2(1.f, 1.f) : make_float2(-1.f, -1.f);
+                reg_op<R, RB>(v, st.a, st.smask, f);
+              } else {
+                OpBflyF f;
+                reg_op<R, RB>(v, st.a, st.smask, f);
+              }
             } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY || pure_swap)) {
               OpRealF f;
-              f.u00 = make_float2(o.uf[0], o.uf[0]); f.u01 = make_float2(o.uf[2], o.uf[2]);
-              f.u10 = make_float2(o.uf[4], o.uf[4]); f.u11 = make_float2(o.uf[6], o.uf[6]);
+              const int k00 = fl ? 6 : 0, k01 = fl ? 4 : 2, k10 = fl ? 2 : 4, k11 = fl ? 0 : 6;
+              f.u00 = make_float2(o.uf[k00], o.uf[k00]); f.u01 = make_float2(o.uf[k01], o.uf[k01]);
+              f.u10 = make_float2(o.uf[k10], o.uf[k10]); f.u11 = make_float2(o.uf[k11], o.uf[k11]);
               reg_op<R, RB>(v, st.a, st.smask, f);
             } else {
-              OpDense<R> f; f.u00 = ucx<R>(o, 0); f.u01 = ucx<R>(o, 1); f.u10 = ucx<R>(o, 2); f.u11 = ucx<R>(o, 3);
+              OpDense<R> f;
+              f.u00 = ucx<R>(o, fl ? 3 : 0); f.u01 = ucx<R>(o, fl ? 2 : 1);
+              f.u10 = ucx<R>(o, fl ? 1 : 2); f.u11 = ucx<R>(o, fl ? 0 : 3);
               reg_op<R, RB>(v, st.a, st.smask, f);
             }
           } else {
@@ -579,7 +634,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
           break;
         }
         case T_LANE:
-          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0, (Prog::kN >= 0)>(v, st, o, lane, tok);
+          lane_op<R, RB, (FEAT & FEAT_SWAP) != 0, (Prog::kN >= 0)>(v, st, o, lane, tok, xl);
           break;
         case T_DIAG_TAB: {
           // a run of register-slot diagonals multiplied out on the host
@@ -604,7 +659,10 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
           const Cx<R> d0 = ucx<R>(o, 0), d1 = ucx<R>(o, 3);
           if (st.type == T_DIAG_REG) {
             if constexpr (sizeof(R) == 4) {
-              reg_diag_rt<R, RB>(v, st.a, st.smask, d0, d1, st.c0 == 0, st.c1 == 0);
+              if (st.pad[1] != 0 && ((xl >> st.pad[2]) & 1))   // relabelled slot: the factors swap sides
+                reg_diag_rt<R, RB>(v, st.a, st.smask, d1, d0, st.c1 == 0, st.c0 == 0);
+              else
+                reg_diag_rt<R, RB>(v, st.a, st.smask, d0, d1, st.c0 == 0, st.c1 == 0);
             } else {
               const int sl = st.a;
 #pragma unroll
@@ -615,7 +673,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
               }
             }
           } else {
-            const bool one = (st.type == T_DIAG_THR) ? ((tl >> st.a) & 1) : ((base & st.gtbit) != 0);
+            const bool one = (st.type == T_DIAG_THR) ? (((tl ^ xl) >> st.a) & 1) : ((base & st.gtbit) != 0);
             const int code = one ? st.c1 : st.c0;
             if (code == 0) break;
             const Cx<R> d = one ? d1 : d0;
@@ -633,7 +691,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
         default: break;
       }
     }
-    store_tile<R, RB>(s, v, base, roff_out, woff_out, lane);
+    store_tile<R, RB>(s, v, base, roff_out, woff_out, gx);
     base = base_nxt;
   }
 }
@@ -642,7 +700,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
 // Op structure as compile-time constants (passes compiled at run time).
 struct OpS {
   uint8_t type, kind, c0, c1, a;
-  uint8_t pad[3];
+  uint8_t pad[3];      // as TOp::pad
   uint32_t smask, tmask;
   uint64_t gmask, gtbit;
 };

@@ -96,8 +96,9 @@ std::string program_of(const TileParams2& P, int sync) {
   for (int i = 0; i < P.nops; ++i) {
     const TOp& o = P.ops[i];
     snprintf(buf, sizeof buf,
-             "      case %d: return OpS{%u, %u, %u, %u, %u, {%u, 0, 0}, %uu, %uu, %lluull, %lluull};\n", i,
+             "      case %d: return OpS{%u, %u, %u, %u, %u, {%u, %u, %u}, %uu, %uu, %lluull, %lluull};\n", i,
              (unsigned)o.type, (unsigned)o.kind, (unsigned)o.c0, (unsigned)o.c1, (unsigned)o.a, (unsigned)o.pad[0],
+             (unsigned)o.pad[1], (unsigned)o.pad[2],
              (unsigned)o.smask, (unsigned)o.tmask, (unsigned long long)o.gmask, (unsigned long long)o.gtbit);
     s += buf;
   }
