@@ -140,13 +140,18 @@ qs_status sim_set_lazy_reset(qs_sim* sim, int on);
 qs_status sim_set_product_start(qs_sim* sim, int on);
 
 /* Arithmetic of the complex128 gate kernels (apply_gate, apply_controlled,
- * circuit_run in every mode): on (nonzero, the default) each FP64 value is
- * held as a double-float pair of FP32 numbers (about 48 significant bits;
- * sums and products by error-free transformations) and computed on the FP32
- * pipes, which this GPU runs at 64 times its FP64 rate; off: on the FP64
- * units.  Amplitudes stay FP64 in memory either way, and both agree with the
- * FP64 oracle to 1e-12.  Reductions and the dense fused gate stay FP64.  The
- * paper's double-precision simulator (Sec. 4.1) computes in FP64. */
+ * circuit_run): 1 holds each FP64 value as a double-float pair of FP32
+ * numbers (about 48 significant bits; sums and products by error-free
+ * transformations) and computes on the FP32 pipes, which this GPU runs at
+ * about 52 times its FP64 rate, in the per-gate sweeps and the tile passes;
+ * 0 computes on the FP64 units everywhere; 2 (the default) takes
+ * double-float in the per-gate sweeps and the FP64 units in the tile passes,
+ * the faster of the two for each as measured on the N = 30 random-gate
+ * circuit.  Gates that only move amplitudes or multiply them by +-1, +-i run
+ * in FP64 in every mode (exact).  Amplitudes stay FP64 in memory, and every
+ * mode agrees with the FP64 oracle to 1e-12.  Reductions and the dense fused
+ * gate stay FP64.  Other values give QS_EINVAL.  The paper's
+ * double-precision simulator (Sec. 4.1) computes in FP64. */
 qs_status sim_set_fp64_emulation(qs_sim* sim, int on);
 
 /* ---- gates (Sec. 2, Eq. (NUM2); Appendix A) ------------------------------ */

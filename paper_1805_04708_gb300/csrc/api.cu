@@ -62,7 +62,7 @@ static qs_status init_handle(qs_sim* s, int N, qs_encoding enc, void* stream) {
   s->zero_pending = false;
   s->lazy_reset = false;
   s->product_start = true;
-  s->c128_df = true;
+  s->c128_df = 2;
   QS_CUDA(cudaGetDevice(&s->device));
   QS_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
   if (enc == QS_ADAPT2) QS_CUDA(cudaMalloc(&s->a2dev, sizeof(A2Dev)));
@@ -203,7 +203,8 @@ extern "C" qs_status qs_set_pipeline_wait_limit(int64_t us) {
 
 extern "C" qs_status sim_set_fp64_emulation(qs_sim* s, int on) {
   QS_TRY(check_sim(s));
-  s->c128_df = on != 0;
+  CHECK_ARG(on >= 0 && on <= 2, "sim_set_fp64_emulation: %d not in 0..2", on);
+  s->c128_df = on;
   return QS_OK;
 }
 

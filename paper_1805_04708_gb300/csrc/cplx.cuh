@@ -98,6 +98,47 @@ template <typename R> __device__ __forceinline__ double2 to_mem(Cx<R> a) {
   return make_double2(to_double(a.x), to_double(a.y));
 }
 
+#ifndef QS_JIT
+// FP64 value -> (hi, lo) with integer operations, the same pair as
+// hi = RN_float(x), lo = RN_float(x - hi) but without the FP64 units: hi is x's
+// significand rounded to 24 bits (to nearest, ties to even); x - hi is the
+// exact integer remainder d (|d| <= 2^28) times 2^(E - 1075), rounded to float
+// by the integer conversion and scaled by two exact powers of two.  Values
+// below 2^-126 in magnitude (no normal float hi) become 0, an absolute error
+// under 1.2e-38; values of 2^76 and more take the FP64 conversion.
+__device__ __forceinline__ DF df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E < 897) return DF(0.f, 0.f);
+  if (E > 1098) return DF(x);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long q = m >> 29;
+  const unsigned long long r = m & 0x1FFFFFFFull;
+  q += (r > 0x10000000ull || (r == 0x10000000ull && (q & 1ull))) ? 1ull : 0ull;
+  const int d = (int)((long long)m - (long long)(q << 29));
+  unsigned int eh = (unsigned int)(E - 896), qh = (unsigned int)q;
+  if (qh == (1u << 24)) { qh >>= 1; ++eh; }
+  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sgn | (eh << 23) | (qh & 0x7FFFFFu));
+  float lo = __fmul_rn(__int2float_rn(d), __uint_as_float((unsigned int)(E - 896) << 23));   // x 2^(E-1023)
+  lo = __fmul_rn(lo, __uint_as_float(75u << 23));                                           // x 2^-52
+  return DF(hi, sgn ? -lo : lo);
+}
+// float -> FP64 from the bits (exact for normal floats; subnormals, which the
+// split above never produces for hi, give 0)
+__device__ __forceinline__ double df_f2d(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long body = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)(e == 0 ? s : (s | body)));
+}
+template <> __device__ __forceinline__ Cx<DF> from_mem<DF>(double2 x) { return cx<DF>(df_split(x.x), df_split(x.y)); }
+template <> __device__ __forceinline__ double2 to_mem<DF>(Cx<DF> a) {
+  return make_double2(__dadd_rn(df_f2d(a.x.hi), df_f2d(a.x.lo)), __dadd_rn(df_f2d(a.y.hi), df_f2d(a.y.lo)));
+}
+#endif
+
 // Storage <-> Cx conversions.
 __device__ __forceinline__ Cx<double> ld(const double2& v) { return cx<double>(v.x, v.y); }
 __device__ __forceinline__ Cx<float> ld(const float2& v) { return cx<float>(v.x, v.y); }

@@ -31,8 +31,8 @@ struct qs_sim {
                       // them first
   bool product_start; // complex64 tile runs from a pending |0..0> start from
                       // the product state of their leading single-qubit gates
-  bool c128_df;       // complex128 tile passes compute in double-float (FP32
-                      // pairs) instead of on the FP64 units
+  int c128_df;        // 0: FP64 units; 1: double-float (FP32 pairs) in every gate kernel;
+                      // 2: double-float in the per-gate sweeps, FP64 units in the tile passes
 };
 // Write a pending |0..0> (no-op otherwise).
 qs_status materialize_state(qs_sim* s);

@@ -233,7 +233,7 @@ qs_status launch_u2(qs_sim* s, const int* controls, int nc, int target, const do
     // run in FP64 and stay exact
     const GateClass gc = classify_u2(u);
     const bool moves = (gc.kind == GK_ANTI || gc.kind == GK_DIAG) && gc.c0 < 4 && gc.c1 < 4;
-    return (s->c128_df && !moves) ? dispatch<DF>(s, controls, nc, target, u)
+    return (s->c128_df != 0 && !moves) ? dispatch<DF>(s, controls, nc, target, u)
                                   : dispatch<double>(s, controls, nc, target, u);
   }
   if (s->enc == QS_C64) return dispatch<float>(s, controls, nc, target, u);

@@ -783,9 +783,31 @@ static qs_status launch_pass(PassSink& k, const TileParams2& P) {
       if (o.type == T_DIAG_TAB) { moves = false; break; }
       moves = (o.kind == GK_ANTI || o.kind == GK_DIAG) && o.c0 < 4 && o.c1 < 4;
     }
-    if (s->c128_df && !moves) {
+    if (s->c128_df == 1 && !moves) {
+      // the coefficients and factor tables as packed (hi, lo) float pairs
+      static thread_local TileParams2 PD;
+      PD = P;
+      auto pack = [](double x) {
+        const float hi = (float)x, lo = (float)(x - (double)hi);
+        uint32_t bh, bl;
+        memcpy(&bh, &hi, 4);
+        memcpy(&bl, &lo, 4);
+        const uint64_t w = (uint64_t)bh | ((uint64_t)bl << 32);
+        double d;
+        memcpy(&d, &w, 8);
+        return d;
+      };
+      for (int i = 0; i < PD.nops; ++i)
+        for (int k = 0; k < 8; ++k) PD.ops[i].ud[k] = pack(P.ops[i].ud[k]);
+      for (int t = 0; t < MAX_TABS; ++t)
+        for (int j = 0; j < 32; ++j) {
+          double x;
+          memcpy(&x, &P.tab[t][j], 8);
+          const double w = pack(x);
+          memcpy(&PD.tab[t][j], &w, 8);
+        }
       QS_CUDA(cudaFuncSetAttribute(k_tile2<DF, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_tile2<DF, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);
+      k_tile2<DF, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, PD);
     } else {
       QS_CUDA(cudaFuncSetAttribute(k_tile2<double, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_tile2<double, 4, 0><<<grid, TPB, smem, s->stream>>>(s->state, P);

@@ -105,7 +105,15 @@ __device__ __forceinline__ uint64_t deposit_t(uint64_t x, uint64_t mask) {
 template <typename R> __device__ __forceinline__ Cx<R> ucx(const TOp& o, int k);
 template <> __device__ __forceinline__ Cx<float> ucx<float>(const TOp& o, int k) { return cx<float>(o.uf[2 * k], o.uf[2 * k + 1]); }
 template <> __device__ __forceinline__ Cx<double> ucx<double>(const TOp& o, int k) { return cx<double>(o.ud[2 * k], o.ud[2 * k + 1]); }
-template <> __device__ __forceinline__ Cx<DF> ucx<DF>(const TOp& o, int k) { return cx<DF>(DF(o.ud[2 * k]), DF(o.ud[2 * k + 1])); }
+// double-float passes: the host stores each coefficient as its (hi, lo) float
+// pair in the 8 bytes of the double (df_pack), so nothing here runs on the
+// FP64 units
+__device__ __forceinline__ DF df_unpack(uint64_t w) {
+  return DF(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)));
+}
+template <> __device__ __forceinline__ Cx<DF> ucx<DF>(const TOp& o, int k) {
+  return cx<DF>(df_unpack(__double_as_longlong(o.ud[2 * k])), df_unpack(__double_as_longlong(o.ud[2 * k + 1])));
+}
 
 // local index of register j under map m, given the thread part tl
 template <int RB>
@@ -194,6 +202,22 @@ __device__ __forceinline__ void reg_op(Cx<R>* v, int s, uint32_t smask, const F&
 
 template <typename R> __device__ __forceinline__ R uscal(const TOp& o) {
   if constexpr (sizeof(R) == 4) return o.uf[0]; else return o.ud[0];
+}
+template <> __device__ __forceinline__ DF uscal<DF>(const TOp& o) { return df_unpack(__double_as_longlong(o.ud[0])); }
+
+// factor of register j in table t (complex64: one (re, im) word; complex128:
+// two FP64 words, or two packed (hi, lo) float pairs in double-float passes)
+template <typename R> __device__ __forceinline__ Cx<R> tab_factor(const TileParams2& P, int t, int j);
+template <> __device__ __forceinline__ Cx<float> tab_factor<float>(const TileParams2& P, int t, int j) {
+  const uint64_t w = P.tab[t][j];
+  return cx<float>(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)));
+}
+template <> __device__ __forceinline__ Cx<double> tab_factor<double>(const TileParams2& P, int t, int j) {
+  return cx<double>(__longlong_as_double((long long)P.tab[t][2 * j]),
+                    __longlong_as_double((long long)P.tab[t][2 * j + 1]));
+}
+template <> __device__ __forceinline__ Cx<DF> tab_factor<DF>(const TileParams2& P, int t, int j) {
+  return cx<DF>(df_unpack(P.tab[t][2 * j]), df_unpack(P.tab[t][2 * j + 1]));
 }
 
 template <typename R> __device__ __forceinline__ R shx(R x, int m);
@@ -640,15 +664,7 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
           // a run of register-slot diagonals multiplied out on the host
 #pragma unroll
           for (int j = 0; j < NR; ++j) {
-            Cx<R> f;
-            if constexpr (sizeof(R) == 4) {
-              const uint64_t w = P.tab[st.a][j];
-              f = cx<R>(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)));
-            } else {
-              f = cx<R>(R(__longlong_as_double((long long)P.tab[st.a][2 * j])),
-                        R(__longlong_as_double((long long)P.tab[st.a][2 * j + 1])));
-            }
-            v[j] = cmul_code(v[j], f, 4);
+            v[j] = cmul_code(v[j], tab_factor<R>(P, st.a, j), 4);
           }
           break;
         }

@@ -267,11 +267,11 @@ def test_shor_config_n30(q, enc):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("df", [True, False])
+@pytest.mark.parametrize("df", [1, 0, 2])
 @pytest.mark.parametrize("N,kind", [(9, "mixed"), (14, "mixed"), (17, "layered"), (20, "gates")])
 def test_c128_tile_passes_fp64_and_double_float(q, df, N, kind, mode):
-    # complex128 tile passes computed on FP32 pairs (double-float, the
-    # default) and on the FP64 units: both within 1e-12 of the oracle
+    # complex128 tile passes computed on FP32 pairs (double-float), on the
+    # FP64 units, and in the default mode: all within 1e-12 of the oracle
     recs = {"mixed": wl.random_mixed_circuit(N, 120, seed=300 + N),
             "layered": wl.layered_circuit(N, 4, seed=N),
             "gates": wl.random_gate_circuit(N, 150, seed=N)}[kind]
