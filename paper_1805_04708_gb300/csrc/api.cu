@@ -155,6 +155,8 @@ extern "C" qs_status sim_destroy(qs_sim* s) {
   if (s->hbuf) cudaFreeHost(s->hbuf);
   if (s->owns && s->state) cudaFree(s->state);
   if (s->a2dev) cudaFree(s->a2dev);
+  for (int i = 0; i < s->evpool_n; ++i) cudaEventDestroy(s->evpool[i]);
+  free(s->evpool);
   delete s;
   if (e != cudaSuccess) {
     qs_set_error("sim_destroy: %s", cudaGetErrorString(e));
@@ -419,19 +421,22 @@ extern "C" qs_status circuit_run_timed(qs_sim* s, const qs_gate* gates, int n, i
                                        float* pass_ms, int max_passes) {
   QS_TRY(check_sim(s));
   CHECK_ARG(max_passes >= 0 && max_passes <= 65536, "circuit_run_timed: max_passes");
+  // the events stay with the handle between calls (creating them is host
+  // work that would otherwise sit between the kernels of every call)
   cudaEvent_t* ev = nullptr;
   int nev = max_passes;
   if (pass_ms && nev > 0) {
-    ev = (cudaEvent_t*)calloc((size_t)2 * nev, sizeof(cudaEvent_t));
-    if (!ev) return QS_ENOMEM;
-    for (int i = 0; i < 2 * nev; ++i) {
-      if (cudaEventCreate(&ev[i]) != cudaSuccess) {
-        for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
-        free(ev);
-        qs_set_error("circuit_run_timed: cudaEventCreate failed");
-        return QS_ECUDA;
-      }
+    if (s->evpool_n < 2 * nev) {
+      cudaEvent_t* p = (cudaEvent_t*)realloc(s->evpool, sizeof(cudaEvent_t) * (size_t)2 * nev);
+      if (!p) return QS_ENOMEM;
+      s->evpool = p;
+      for (; s->evpool_n < 2 * nev; ++s->evpool_n)
+        if (cudaEventCreate(&s->evpool[s->evpool_n]) != cudaSuccess) {
+          qs_set_error("circuit_run_timed: cudaEventCreate failed");
+          return QS_ECUDA;
+        }
     }
+    ev = s->evpool;
   }
   int np = 0;
   qs_status st = run_gates(s, gates, n, mode, &np, ev, nev);
@@ -448,8 +453,6 @@ extern "C" qs_status circuit_run_timed(qs_sim* s, const qs_gate* gates, int n, i
       }
       pass_ms[i] = ms;
     }
-    for (int i = 0; i < 2 * nev; ++i) cudaEventDestroy(ev[i]);
-    free(ev);
   }
   if (n_passes) *n_passes = np;
   return st;

@@ -17,6 +17,8 @@ struct qs_sim {
   bool owns;          // state allocated by the handle
   void* a2dev;        // ADAPT2: device A2Dev block (current and next magnitude range)
   void* scratch;      // device scratch for reductions and ADAPT2 range passes
+  cudaEvent_t* evpool = nullptr;   // circuit_run_timed's per-pass events, kept between calls
+  int evpool_n = 0;
   size_t scratch_bytes;
   void* hbuf;         // pinned host staging for results
   size_t hbuf_bytes;

@@ -474,7 +474,7 @@ class Sim:
         _check(_lib.circuit_run(self._h, arr, n, int(mode), ctypes.byref(npass)))
         return npass.value
 
-    def circuit_run_timed(self, gates, mode=1, max_passes=4096):
+    def circuit_run_timed(self, gates, mode=1, max_passes=256):
         """As circuit_run; returns the device time (ms) of every sweep."""
         if isinstance(gates, tuple):
             arr, n = gates
