@@ -243,6 +243,25 @@ struct OpBflyS {
     a1 = cx<float>(B1.x, B1.y);
   }
 };
+// The unscaled butterfly computed in place, for a loop that keeps its values
+// in fixed registers (no temporaries, hence no moves): a0 <- a0 + a1, then
+// a1 <- a0_new - 2 a1 = a0 - a1 (one more rounding than the direct form).
+// With SW the pair's roles are exchanged (a relabelled index bit).
+template <bool SW> struct OpBflyIP {
+  __device__ __forceinline__ void pair(Cx<float>& a0, Cx<float>& a1) const {
+    Cx<float>& p = SW ? a1 : a0;
+    Cx<float>& q = SW ? a0 : a1;
+#ifdef QS_HAVE_F32X2
+    const float2 P = __fadd2_rn(make_float2(p.x, p.y), make_float2(q.x, q.y));
+    p = cx<float>(P.x, P.y);
+    const float2 Q = __ffma2_rn(make_float2(-2.f, -2.f), make_float2(q.x, q.y), P);
+    q = cx<float>(Q.x, Q.y);
+#else
+    p = cx<float>(p.x + q.x, p.y + q.y);
+    q = cx<float>(fmaf(-2.f, q.x, p.x), fmaf(-2.f, q.y, p.y));
+#endif
+  }
+};
 template <typename R> struct OpMul {
   Cx<R> f; int c;
   __device__ __forceinline__ void one(Cx<R>& a) const { a = cmul_code(a, f, c); }

@@ -631,6 +631,15 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
                 OpBflyF f;
                 reg_op<R, RB>(v, st.a, st.smask, f);
               }
+            } else if ((FEAT & FEAT_HAD) && Prog::kN < 0 && st.kind == GK_BFLY) {
+              // the interpreter: in place, no register moves
+              if (fl) {
+                OpBflyIP<true> f;
+                reg_op<R, RB>(v, st.a, st.smask, f);
+              } else {
+                OpBflyIP<false> f;
+                reg_op<R, RB>(v, st.a, st.smask, f);
+              }
             } else if ((FEAT & FEAT_HAD) && (st.kind == GK_REAL || st.kind == GK_BFLY || pure_swap)) {
               OpRealF f;
               const int k00 = fl ? 6 : 0, k01 = fl ? 4 : 2, k10 = fl ? 2 : 4, k11 = fl ? 0 : 6;
