@@ -49,7 +49,7 @@ UNIT = "updates/s"
 # interpreter and compiled passes), as the mean over a step's 8 passes of
 # which the first only writes, scaled by the 16x units; None when a pass
 # kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = 1.5213e10
+TILE_TRAFFIC_PER_PASS = 1.5220e10
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
@@ -552,6 +552,7 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
     s = qsim.Sim(N, "c64", stream=stream)
     s.circuit_run(gates, mode=1)
     st = {}
+    s.measure(5, 0.3)   # the first call allocates the handle's scratch and host buffers
     ms, out = _timed(torch, stream, lambda: s.measure(7, 0.3))
     st["M_ms"] = ms
     try:
