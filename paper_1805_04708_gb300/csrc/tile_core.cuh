@@ -228,9 +228,8 @@ template <> __device__ __forceinline__ DF shx<DF>(DF x, int m) {
 }
 
 // lane-bit op: partner values by shuffle, each lane keeps its own output
-// CT: the op's structure is a compile-time constant (compiled passes), which
-// enables the butterfly form of GK_BFLY; the interpreter runs GK_BFLY as the
-// real matrix [[1, 1], [1, -1]] that its coefficients hold.
+// (GK_BFLY as the butterfly: one packed instruction per amplitude, written in
+// place).  CT: the op's structure is a compile-time constant (compiled passes).
 template <typename R, int RB, bool SWAP, bool CT, class OS>
 __device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, int lane, bool tok, uint32_t xl) {
   const int m = 1 << st.a;
@@ -246,7 +245,7 @@ __device__ __forceinline__ void lane_op(Cx<R>* v, const OS& st, const TOp& o, in
       }
       return;
     }
-    if (CT && st.kind == GK_BFLY) {
+    if (st.kind == GK_BFLY) {
       // butterfly: own + partner (low lane), partner - own (high lane)
       const float2 sg = hi ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
 #pragma unroll
