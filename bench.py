@@ -447,7 +447,7 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
     torch.cuda.empty_cache()
 
     s128 = qsim.Sim(N, "c128", stream=stream)
-    for df, suffix in ((2, ""), (1, "_double_float"), (0, "_fp64_units")):
+    for df, suffix in ((1, ""), (2, "_df_sweeps_fp64_passes"), (0, "_fp64_units")):
         s128.set_fp64_emulation(df)
         for mode, key in ((1, "c128_tile_passes"), (0, "c128_per_gate_sweeps")):
             def run128(mode=mode):
@@ -456,9 +456,10 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
             run128()
             ms, _ = _timed(torch, stream, run128)
             v[key + suffix] = {"value": upd_per_step / (ms / 1e3), "ms_per_circuit": ms,
-                               "arithmetic": {2: "default (double-float per-gate sweeps, FP64 tile passes)",
-                                              1: "double-float on FP32 pipes", 0: "FP64 units"}[df]}
-    s128.set_fp64_emulation(2)
+                               "arithmetic": {1: "double-float on FP32 pipes (default)",
+                                              2: "double-float per-gate sweeps, FP64 tile passes",
+                                              0: "FP64 units"}[df]}
+    s128.set_fp64_emulation(1)
     s128.close()
     del s128
     torch.cuda.empty_cache()

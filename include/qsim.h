@@ -140,14 +140,13 @@ qs_status sim_set_lazy_reset(qs_sim* sim, int on);
 qs_status sim_set_product_start(qs_sim* sim, int on);
 
 /* Arithmetic of the complex128 gate kernels (apply_gate, apply_controlled,
- * circuit_run): 1 holds each FP64 value as a double-float pair of FP32
- * numbers (about 48 significant bits; sums and products by error-free
- * transformations) and computes on the FP32 pipes, which this GPU runs at
- * about 52 times its FP64 rate, in the per-gate sweeps and the tile passes;
- * 0 computes on the FP64 units everywhere; 2 (the default) takes
- * double-float in the per-gate sweeps and the FP64 units in the tile passes,
- * the faster of the two for each as measured on the N = 30 random-gate
- * circuit.  Gates that only move amplitudes or multiply them by +-1, +-i run
+ * circuit_run): 1 (the default) holds each FP64 value as a double-float pair
+ * of FP32 numbers (about 48 significant bits; products by an error-free
+ * transformation, sums with an exact sum of the high parts) and computes on
+ * the FP32 pipes, which this GPU runs at about 52 times its FP64 rate, in the
+ * per-gate sweeps and the tile passes; 0 computes on the FP64 units
+ * everywhere; 2 takes double-float in the per-gate sweeps and the FP64 units
+ * in the tile passes.  Gates that only move amplitudes or multiply them by +-1, +-i run
  * in FP64 in every mode (exact).  Amplitudes stay FP64 in memory, and every
  * mode agrees with the FP64 oracle to 1e-12.  Reductions and the dense fused
  * gate stay FP64.  Other values give QS_EINVAL.  The paper's

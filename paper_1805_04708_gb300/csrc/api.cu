@@ -62,7 +62,7 @@ static qs_status init_handle(qs_sim* s, int N, qs_encoding enc, void* stream) {
   s->zero_pending = false;
   s->lazy_reset = false;
   s->product_start = true;
-  s->c128_df = 2;
+  s->c128_df = 1;
   QS_CUDA(cudaGetDevice(&s->device));
   QS_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
   if (enc == QS_ADAPT2) QS_CUDA(cudaMalloc(&s->a2dev, sizeof(A2Dev)));

@@ -42,11 +42,14 @@ __device__ __forceinline__ DF df_two_sum(float a, float b) {
   const float bb = __fsub_rn(s, a);
   return DF(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
+// The sum: TwoSum of the high parts (exact), the low parts added in FP32, one
+// renormalisation.  Its error is within a few units of 2^-44 of the larger
+// operand (the low parts' rounding), far inside what the complex128 paths
+// need (1e-12 absolute on amplitudes of magnitude <= 1), at about half the
+// instructions of a second TwoSum on the low parts.
 __device__ __forceinline__ DF operator+(DF a, DF b) {
-  DF s = df_two_sum(a.hi, b.hi);
-  const DF t = df_two_sum(a.lo, b.lo);
-  s = df_quick(s.hi, __fadd_rn(s.lo, t.hi));
-  return df_quick(s.hi, __fadd_rn(s.lo, t.lo));
+  const DF s = df_two_sum(a.hi, b.hi);
+  return df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
 __device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }

@@ -448,10 +448,10 @@ class Sim:
         sim_set_product_start); on by default."""
         _check(_lib.sim_set_product_start(self._h, 1 if on else 0))
 
-    def set_fp64_emulation(self, on=2):
-        """complex128 gate arithmetic: True / 1 double-float everywhere, False /
-        0 FP64 units everywhere, 2 (default) double-float in the per-gate
-        sweeps and FP64 units in the tile passes."""
+    def set_fp64_emulation(self, on=1):
+        """complex128 gate arithmetic: True / 1 (default) double-float
+        everywhere, False / 0 FP64 units everywhere, 2 double-float in the
+        per-gate sweeps and FP64 units in the tile passes."""
         _check(_lib.sim_set_fp64_emulation(self._h, int(on)))
 
     def apply_permutation(self, controls, reg_lo, reg_w, table):
