@@ -60,7 +60,17 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_quick(p, e);
 }
-__device__ __forceinline__ DF fma(DF a, DF b, DF c) { return a * b + c; }
+// a * b + c with one renormalisation: the product's high part and its
+// error-free remainder (TwoProd), the exact sum of the high parts (TwoSum),
+// the low terms added in FP32
+__device__ __forceinline__ DF fma(DF a, DF b, DF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const DF s = df_two_sum(p, c.hi);
+  return df_quick(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
 __device__ __forceinline__ bool operator!=(DF a, DF b) { return a.hi != b.hi || a.lo != b.lo; }
 
 template <typename R> struct __align__(2 * sizeof(R)) Cx { R x, y; };
@@ -76,7 +86,7 @@ __device__ __forceinline__ Cx<R> cmul_code(Cx<R> a, Cx<R> f, int code) {
     case 1: return cx<R>(-a.y, a.x);
     case 2: return cx<R>(-a.x, -a.y);
     case 3: return cx<R>(a.y, -a.x);
-    default: return cx<R>(a.x * f.x - a.y * f.y, a.x * f.y + a.y * f.x);
+    default: return cx<R>(fma(a.x, f.x, -(a.y * f.y)), fma(a.x, f.y, a.y * f.x));
   }
 }
 
