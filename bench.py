@@ -49,7 +49,7 @@ UNIT = "updates/s"
 # interpreter and compiled passes), as the mean over a step's 8 passes of
 # which the first only writes, scaled by the 16x units; None when a pass
 # kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = 1.5220e10
+TILE_TRAFFIC_PER_PASS = 1.5227e10
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
