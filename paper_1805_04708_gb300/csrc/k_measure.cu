@@ -12,7 +12,8 @@
 // smallest index i with C_i > u_k C_last, C_i = sum_{j <= i} |a_j|^2.  Three
 // sweeps of small arrays after one read of the state:
 //   k_ev_chunks  : FP64 sum of |a|^2 over each chunk of 1024 amplitudes
-//                  (one warp per chunk; products exact for complex64);
+//                  (one warp per chunk; each lane's squares exact and summed
+//                  in float-float for complex64 and the adaptive encoding);
 //   k_scan_*     : exclusive prefix of the chunk sums in a fixed tree order;
 //   k_ev_sample  : one warp per event: binary search of the chunk prefix for
 //                  the first chunk whose end exceeds the target, then the
@@ -82,6 +83,46 @@ __device__ __forceinline__ double warp_incl_scan(double x, int lane) {
   return x;
 }
 
+// a lane's sum of squares in float-float: each square formed exactly (p + e
+// by FMA) and added with a TwoSum, so the FP64 units do nothing per amplitude
+struct SqAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_sq(float a) {
+    const float p = __fmul_rn(a, a);
+    const float e = __fmaf_rn(a, a, -p);
+    const float t = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+    lo = __fadd_rn(lo, e);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <typename A>
+__device__ __forceinline__ double lane_chunk_sum(const A* s, uint64_t i0, uint64_t len, int lane, const float* r) {
+  double acc = 0.0;
+  for (uint64_t j = lane; j < len; j += 32) acc += Prob<A>::at(s, i0 + j, r);
+  return acc;
+}
+template <>
+__device__ __forceinline__ double lane_chunk_sum<float2>(const float2* s, uint64_t i0, uint64_t len, int lane,
+                                                         const float*) {
+  SqAcc f;
+  for (uint64_t j = lane; j < len; j += 32) {
+    const float2 a = s[i0 + j];
+    f.add_sq(a.x);
+    f.add_sq(a.y);
+  }
+  return f.value();
+}
+template <>
+__device__ __forceinline__ double lane_chunk_sum<uint16_t>(const uint16_t* s, uint64_t i0, uint64_t len, int lane,
+                                                           const float* r) {
+  SqAcc f;
+  for (uint64_t j = lane; j < len; j += 32) f.add_sq(r[(s[i0 + j] & 0xFFu) ^ 0x80u]);
+  return f.value();
+}
+
 // chunk sums: one warp per chunk of 2^clog amplitudes; lane l sums the
 // amplitudes l, l + 32, ... of the chunk (coalesced), then a warp tree
 template <typename A>
@@ -94,8 +135,7 @@ __global__ void __launch_bounds__(TPB) k_ev_chunks(const A* __restrict__ s, uint
   const uint64_t nw = ((uint64_t)gridDim.x * TPB) >> 5;
   const uint64_t len = 1ull << clog;
   for (uint64_t c = w0; c < nchunks; c += nw) {
-    double acc = 0.0;
-    for (uint64_t j = lane; j < len; j += 32) acc += Prob<A>::at(s, (c << clog) + j, L.r);
+    double acc = lane_chunk_sum<A>(s, c << clog, len, lane, L.r);
     acc = warp_sum(acc);
     if (lane == 0) sums[c] = acc;
   }
