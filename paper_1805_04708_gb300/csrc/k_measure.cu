@@ -141,6 +141,24 @@ __global__ void __launch_bounds__(TPB) k_ev_chunks(const A* __restrict__ s, uint
   }
 }
 
+// CLEAR / SET and the projection of M: on every pair of Eq. (NUM2) along
+// qubit q, the element with bit q = `bit` is scaled by c and the other is set
+// to zero without being read (one read of half the state, one write of all).
+template <typename A, typename F>
+__global__ void __launch_bounds__(TPB) k_project(A* __restrict__ s, uint64_t npairs, int q, int bit, F c) {
+  const uint64_t low = (1ull << q) - 1, qb = 1ull << q;
+  const uint64_t stride = (uint64_t)gridDim.x * TPB;
+  for (uint64_t j = (uint64_t)blockIdx.x * TPB + threadIdx.x; j < npairs; j += stride) {
+    const uint64_t i0 = ((j & ~low) << 1) | (j & low);
+    const uint64_t keep = bit ? (i0 | qb) : i0;
+    A a = s[keep];
+    a.x *= c;
+    a.y *= c;
+    s[keep] = a;
+    s[keep ^ qb] = A{};
+  }
+}
+
 // block-level exclusive scan of one value per thread (Kogge-Stone in shared
 // memory, fixed order); returns the exclusive prefix, *total the block sum
 __device__ double block_excl_scan(double x, double* total) {
@@ -379,11 +397,20 @@ extern "C" qs_status generate_events_seeded(qs_sim* s, uint64_t seed, int64_t n,
 // projection onto `bit` of qubit q, scaled by c (a diagonal update with the
 // entries (c, 0) or (0, c) on the pair of Eq. (NUM2))
 static qs_status project_scaled(qs_sim* s, int q, int bit, double c) {
-  double u[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (bit == 0) u[0] = c; else u[6] = c;
-  if (s->enc == QS_ADAPT2) return a2_apply_arith(s, nullptr, 0, q, u);
+  if (s->enc == QS_ADAPT2) {
+    double u[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (bit == 0) u[0] = c; else u[6] = c;
+    return a2_apply_arith(s, nullptr, 0, q, u);
+  }
   QS_TRY(materialize_state(s));
-  return launch_u2(s, nullptr, 0, q, u);
+  const uint64_t npairs = 1ull << (s->N - 1);
+  const unsigned grid = grid_for(s, (npairs + 31) / 32);
+  if (s->enc == QS_C128)
+    k_project<double2, double><<<grid, TPB, 0, s->stream>>>((double2*)s->state, npairs, q, bit, c);
+  else
+    k_project<float2, float><<<grid, TPB, 0, s->stream>>>((float2*)s->state, npairs, q, bit, (float)c);
+  QS_LAUNCH_CHECK();
+  return QS_OK;
 }
 
 static qs_status qubit_probs(qs_sim* s, int q, double* p0, double* p1) {
