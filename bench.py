@@ -785,7 +785,7 @@ def run_gpu(args):
 
     # end to end through the public API: gate records from host memory each
     # step, results (norm, 3N expectation values) read back to the host
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
