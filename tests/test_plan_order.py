@@ -24,11 +24,13 @@ def rand_state(N, seed):
     return v / np.linalg.norm(v)
 
 
+@pytest.mark.parametrize("enc", ["c64", "c128"])
 @pytest.mark.parametrize("N,kind,seed", [(13, "mixed", 1), (14, "mixed", 2), (14, "gate", 3), (16, "gate", 4)])
-def test_planned_order_gives_the_same_state(q, N, kind, seed):
+def test_planned_order_gives_the_same_state(q, N, kind, seed, enc):
+    # both encodings' planners move commuting gates ahead into earlier passes
     recs = (wl.random_mixed_circuit(N, 150, seed=seed) if kind == "mixed"
             else wl.random_gate_circuit(N, 150, seed=seed, hadamard_layer=False))
-    passes = q.circuit_plan(N, recs, "c64")
+    passes = q.circuit_plan(N, recs, enc)
     order = [i for p in passes for i in p]
     assert sorted(order) == sorted(set(order))            # each gate at most once
     dropped = set(range(len(recs))) - set(order)          # only identities may be dropped
@@ -42,13 +44,6 @@ def test_planned_order_gives_the_same_state(q, N, kind, seed):
     ref = circuit.run(v0.copy(), N, recs)
     got = circuit.run(v0.copy(), N, [recs[i] for i in order])
     assert np.max(np.abs(got - ref)) <= 1e-12
-
-
-def test_complex128_keeps_circuit_order(q):
-    N = 14
-    recs = wl.random_gate_circuit(N, 120, seed=8, hadamard_layer=False)
-    order = [i for p in q.circuit_plan(N, recs, "c128") for i in p]
-    assert order == sorted(order)
 
 
 def test_plan_rejects(q):
