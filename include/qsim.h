@@ -129,7 +129,8 @@ qs_status sim_reset(qs_sim* sim);
 qs_status sim_set_lazy_reset(qs_sim* sim, int on);
 
 /* Product start (on: nonzero; default on).  When circuit_run (modes 1-3) of a
- * complex64 state starts from a pending |0..0>, every single-qubit gate that
+ * complex64 or complex128 state starts from a pending |0..0>, every
+ * single-qubit gate that
  * comes before all multi-qubit gates on its qubit acts on an unentangled
  * qubit and commutes with every earlier gate on other qubits; these gates are
  * composed per qubit (FP64) and the first tile pass writes the product state
@@ -244,8 +245,9 @@ qs_status shorbox_init(qs_sim* sim, int nx, uint64_t G, uint64_t y);
  * Modes 2 and 3 give QS_EUNSUPPORTED on a QS_C64 state when NVRTC cannot be
  * loaded; QS_C128 states use the interpreter in every tile mode.  For
  * QS_C64, a last pass of at most 4 gates joins the previous pass when their
- * targets fit its tile, and a run from a pending |0..0> starts from the
- * product state of its leading single-qubit gates (sim_set_product_start).
+ * targets fit its tile; for QS_C64 and QS_C128 a run from a pending |0..0>
+ * starts from the product state of its leading single-qubit gates
+ * (sim_set_product_start).
  * Results equal mode 0 up to floating-point rounding order.  gates: host
  * array of n records.  n_passes (may be NULL) receives the number of state
  * sweeps launched.  The paper has no counterpart for modes 1-3. */

@@ -31,7 +31,7 @@ struct qs_sim {
                       // tile pass makes its tiles instead of loading them,
                       // every other call that touches the amplitudes writes
                       // them first
-  bool product_start; // complex64 tile runs from a pending |0..0> start from
+  bool product_start; // tile runs from a pending |0..0> start from
                       // the product state of their leading single-qubit gates
   int c128_df;        // 0: FP64 units; 1: double-float (FP32 pairs) in every gate kernel;
                       // 2: double-float in the per-gate sweeps, FP64 units in the tile passes

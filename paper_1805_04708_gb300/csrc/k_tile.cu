@@ -509,7 +509,7 @@ struct PassSink {
   std::vector<JitJob>* collect;   // compile only: the kernels to compile
   std::vector<int>* plan;         // plan only: gate indices in run order
   std::vector<int>* plan_start;   // plan only: first index of each pass
-  const double (*prod)[2][2];     // complex64 run from a pending |0..0>: the
+  const double (*prod)[2][2];     // a run from a pending |0..0>: the
                                   // product start f[q][bit] = (re, im), or null
 };
 
@@ -568,12 +568,19 @@ static uint64_t f2_bits_host(double re, double im) {
   return (uint64_t)br | ((uint64_t)bi << 32);
 }
 
-// The product start of a complex64 pass: per-qubit factors and the register
-// table of the load map (products in FP64, rounded once).
-static void fill_product(TileParams2& P, const double (*f)[2][2], int RB) {
+// The product start of a pass: per-qubit factors and the register table of
+// the load map (products in FP64, rounded once for complex64; kept in FP64,
+// pfd and ptabd, for complex128).
+static void fill_product(TileParams2& P, const double (*f)[2][2], int RB, bool fp64) {
   P.from_product = 1;
   for (int q = 0; q < P.N; ++q)
-    for (int bit = 0; bit < 2; ++bit) P.pf[q][bit] = f2_bits_host(f[q][bit][0], f[q][bit][1]);
+    for (int bit = 0; bit < 2; ++bit) {
+      P.pf[q][bit] = f2_bits_host(f[q][bit][0], f[q][bit][1]);
+      if (fp64) {
+        memcpy(&P.pfd[q][bit][0], &f[q][bit][0], 8);
+        memcpy(&P.pfd[q][bit][1], &f[q][bit][1], 8);
+      }
+    }
   for (int j = 0; j < (1 << RB); ++j) {
     double tr = 1.0, ti = 0.0;
     for (int sl = 0; sl < RB; ++sl) {
@@ -585,6 +592,10 @@ static void fill_product(TileParams2& P, const double (*f)[2][2], int RB) {
       tr = r;
     }
     P.ptab[j] = f2_bits_host(tr, ti);
+    if (fp64 && j < 16) {
+      memcpy(&P.ptabd[j][0], &tr, 8);
+      memcpy(&P.ptabd[j][1], &ti, 8);
+    }
   }
 }
 
@@ -707,7 +718,7 @@ qs_status run_tile_passes(qs_sim* s, const qs_gate* gates, int n, int* n_passes,
   qs_status st;
   static thread_local double prod[64][2][2];
   static thread_local std::vector<qs_gate> rest;
-  if (s->enc == QS_C64 && s->zero_pending && s->product_start &&
+  if ((s->enc == QS_C64 || s->enc == QS_C128) && s->zero_pending && s->product_start &&
       product_prefix(s->N, gates, n, prod, &rest) > 0) {
     k.prod = prod;
     // the gates after the prefix may all be identities, which the planner
@@ -874,7 +885,7 @@ static qs_status run_pass(PassSink& k, const qs_gate* gates, const int* gidx, in
     // instead of being loaded
     P.from_zero = (k.s && k.s->zero_pending) ? 1 : 0;
     P.from_product = 0;
-    if (P.from_zero && k.prod) fill_product(P, k.prod, tile_register_bits(k.enc));
+    if (P.from_zero && k.prod) fill_product(P, k.prod, tile_register_bits(k.enc), k.enc == QS_C128);
     QS_TRY(emit_pass(k, P));
     if (P.from_zero) k.s->zero_pending = false;
     return QS_OK;

@@ -79,13 +79,17 @@ struct TileParams2 {
   int last_xpose;      // index of the last transpose op, -1 if none
   int from_zero;       // the state is |0..0> and not in memory: tiles start as
                        // zeros (amplitude 1 at index 0), nothing is loaded
-  // complex64, with from_zero: tiles start as the product state
+  // with from_zero: tiles start as the product state
   // a(i) = prod_q f_q(bit q of i) instead (f_q = (1, 0) for every q is |0..0>).
-  // pf[q][bit]: f_q(bit) as float2 bits; ptab[j]: the product over the
-  // register slots of the load map for register j, formed in FP64
+  // complex64: pf[q][bit] = f_q(bit) as float2 bits; ptab[j] = the product
+  // over the register slots of the load map for register j, formed in FP64.
+  // complex128: the same in FP64, pfd[q][bit] = (re, im) and ptabd[j] =
+  // (re, im) as double bits
   int from_product;
   uint64_t pf[64][2];
   uint64_t ptab[32];
+  uint64_t pfd[64][2][2];
+  uint64_t ptabd[16][2];
   TOp ops[MAX_TOPS];   // T_XPOSE ops carry their new map in the next TMap slot
   TMap maps[16];
   // T_DIAG_TAB: the factor of register j, complex64 (re, im) float bits in
@@ -391,6 +395,14 @@ __device__ __forceinline__ Cx<float> f2_bits(uint64_t u) {
   return cx<float>(__uint_as_float((unsigned)(u & 0xFFFFFFFFu)), __uint_as_float((unsigned)(u >> 32)));
 }
 __device__ __forceinline__ Cx<float> pf_at(const TileParams2& P, int q, int bit) { return f2_bits(P.pf[q][bit]); }
+// complex128 product-start helpers (FP64)
+__device__ __forceinline__ double2 pfd_at(const TileParams2& P, int q, int bit) {
+  return make_double2(__longlong_as_double((long long)P.pfd[q][bit][0]),
+                      __longlong_as_double((long long)P.pfd[q][bit][1]));
+}
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
 __device__ __forceinline__ Cx<float> cmul_f(Cx<float> a, Cx<float> b) {
   return cx<float>(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -465,14 +477,16 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
   const bool load = !P.from_zero;
   // product start: the factor of this thread's lane and warp bits
   Cx<float> fthr = cx<float>(1.f, 0.f);
-  if (sizeof(R) == 4 && P.from_product) {
+  double2 fthr_d = make_double2(1.0, 0.0);
+  if (P.from_product) {
     for (int k = 1; k < P.b; ++k) {
       bool is_reg = false;
 #pragma unroll
       for (int sl = 0; sl < RB; ++sl) is_reg |= (P.init.reg[sl] == k);
       if (is_reg) continue;
       const int q = k < 4 ? k : P.gpos[k];
-      fthr = cmul_f(fthr, pf_at(P, q, (tl_in >> k) & 1));
+      if constexpr (sizeof(R) == 4) fthr = cmul_f(fthr, pf_at(P, q, (tl_in >> k) & 1));
+      else fthr_d = cmul_d(fthr_d, pfd_at(P, q, (tl_in >> k) & 1));
     }
   }
   // tile tau starts at base = deposit(tau) (its bits spread over the bits
@@ -488,18 +502,32 @@ __device__ __forceinline__ void tile_pass(void* __restrict__ s, const TileParams
     if (load) {
       cp_async_wait_all();
       unstage_tile<R, RB>(stg, v, lreg_in, tl_in);
-    } else if (sizeof(R) == 4 && P.from_product) {
+    } else if (P.from_product) {
       // product state: thread factor x the factors of the qubits outside the
       // tile x the register table
-      Cx<float> f = fthr;
-      for (uint64_t m = P.out_mask; m; m &= m - 1) {
-        const int q = __ffsll((long long)m) - 1;
-        f = cmul_f(f, pf_at(P, q, (int)((base >> q) & 1)));
-      }
+      if constexpr (sizeof(R) == 4) {
+        Cx<float> f = fthr;
+        for (uint64_t m = P.out_mask; m; m &= m - 1) {
+          const int q = __ffsll((long long)m) - 1;
+          f = cmul_f(f, pf_at(P, q, (int)((base >> q) & 1)));
+        }
 #pragma unroll
-      for (int j = 0; j < NR; ++j) {
-        const Cx<float> t = cmul_f(f, f2_bits(P.ptab[j]));
-        v[j] = cx<R>((R)t.x, (R)t.y);
+        for (int j = 0; j < NR; ++j) {
+          const Cx<float> t = cmul_f(f, f2_bits(P.ptab[j]));
+          v[j] = cx<R>((R)t.x, (R)t.y);
+        }
+      } else {
+        double2 f = fthr_d;
+        for (uint64_t m = P.out_mask; m; m &= m - 1) {
+          const int q = __ffsll((long long)m) - 1;
+          f = cmul_d(f, pfd_at(P, q, (int)((base >> q) & 1)));
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          const double2 t = cmul_d(f, make_double2(__longlong_as_double((long long)P.ptabd[j][0]),
+                                                   __longlong_as_double((long long)P.ptabd[j][1])));
+          v[j] = from_mem<R>(t);
+        }
       }
     } else {
       // |0..0>: register 0 of thread 0 of the tile at base 0 is index 0
