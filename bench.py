@@ -459,6 +459,23 @@ def run_variants(qsim, torch, stream, sim, gates, upd_per_step, N, mode=1):
                                "arithmetic": {1: "double-float on FP32 pipes (default)",
                                               2: "double-float per-gate sweeps, FP64 tile passes",
                                               0: "FP64 units"}[df]}
+    # the dense fused gate in complex128 (CUDA cores): k = 2..5 on the k lowest
+    # and on spread qubits, double-float and FP64 units
+    fused128 = {}
+    for df, arith in ((1, "double_float"), (0, "fp64_units")):
+        s128.set_fp64_emulation(df)
+        for k in (2, 3, 4, 5):
+            g = np.random.default_rng(k)
+            Z = g.standard_normal((1 << k, 1 << k)) + 1j * g.standard_normal((1 << k, 1 << k))
+            Qm, Rm = np.linalg.qr(Z)
+            U = Qm * (np.diag(Rm) / np.abs(np.diag(Rm)))
+            for qs, where in ((list(range(k)), "low"), ([3, 9, 17, 22, 29][:k], "spread")):
+                s128.apply_fused(qs, U)
+                ms, _ = _timed(torch, stream, lambda: s128.apply_fused(qs, U))
+                fused128["%s_k%d_%s" % (arith, k, where)] = {
+                    "ms": ms, "GB/s": 2.0 * (16 << N) / (ms / 1e3) / 1e9,
+                    "complex_fma_T/s": (1 << k) * float(1 << N) / (ms / 1e3) / 1e12}
+    v["fused_dense_c128_n30"] = fused128
     s128.set_fp64_emulation(1)
     s128.close()
     del s128

@@ -2,7 +2,9 @@
 // 2^k amplitudes that differ only in the qubits `qubits` is multiplied by the
 // 2^k x 2^k matrix (Eq. (AQS0) for n-qubit gates; the fused multi-qubit gates
 // proposed at the end of Sec. 5.2).  CUDA-core version: one thread per group,
-// the group staged in shared memory, the matrix in shared memory.
+// the group staged in shared memory, the matrix in shared memory.  complex128
+// computes in double-float on the FP32 pipes unless the handle asks for the
+// FP64 units (sim_set_fp64_emulation 0).
 #include "internal.cuh"
 #include "cplx.cuh"
 #include <string.h>
@@ -17,13 +19,21 @@ struct FusedGeo {
   int qpos[5];       // qubits in local-bit order: local bit m <-> qubits[m]
 };
 
+// an amplitude from memory in the arithmetic type R, and back
+template <typename R> __device__ __forceinline__ Cx<R> ld_amp(float2 v) { return cx<R>(v.x, v.y); }
+template <typename R> __device__ __forceinline__ Cx<R> ld_amp(double2 v) { return from_mem<R>(v); }
+template <typename R> __device__ __forceinline__ void st_amp(float2* p, Cx<R> a) { *p = make_float2(a.x, a.y); }
+template <typename R> __device__ __forceinline__ void st_amp(double2* p, Cx<R> a) { *p = to_mem<R>(a); }
+
 template <typename R, typename A>
 __global__ void __launch_bounds__(TPB) k_fused(A* __restrict__ s, FusedGeo g, const double* __restrict__ U) {
   extern __shared__ unsigned char smraw[];
   const int d = 1 << g.k;
   Cx<R>* M = (Cx<R>*)smraw;                       // d*d
-  Cx<R>* buf = M + d * d + threadIdx.x * d;        // per-thread group
-  for (int i = threadIdx.x; i < d * d; i += TPB) M[i] = cx<R>((R)U[2 * i], (R)U[2 * i + 1]);
+  // this thread's group: element c at buf[c * TPB], so that the lanes of a
+  // warp read neighbouring words (no bank conflicts)
+  Cx<R>* buf = M + d * d + threadIdx.x;
+  for (int i = threadIdx.x; i < d * d; i += TPB) M[i] = cx<R>(R(U[2 * i]), R(U[2 * i + 1]));
   __syncthreads();
   const uint64_t ngroups = 1ull << (g.N - g.k);
   const uint64_t grp = (uint64_t)blockIdx.x * TPB + threadIdx.x;
@@ -36,19 +46,15 @@ __global__ void __launch_bounds__(TPB) k_fused(A* __restrict__ s, FusedGeo g, co
     for (int m = 0; m < g.k; ++m) o |= (uint64_t)((c >> m) & 1) << g.qpos[m];
     lofs[c] = o;
   }
-  for (int c = 0; c < d; ++c) {
-    A v = s[base | lofs[c]];
-    buf[c] = cx<R>(v.x, v.y);
-  }
+  for (int c = 0; c < d; ++c) buf[c * TPB] = ld_amp<R>(s[base | lofs[c]]);
   for (int r = 0; r < d; ++r) {
-    R re = 0, im = 0;
+    R re = R(0), im = R(0);
     for (int c = 0; c < d; ++c) {
-      Cx<R> u = M[r * d + c], a = buf[c];
+      Cx<R> u = M[r * d + c], a = buf[c * TPB];
       re = fma(u.x, a.x, re); re = fma(-u.y, a.y, re);
       im = fma(u.x, a.y, im); im = fma(u.y, a.x, im);
     }
-    A o; o.x = re; o.y = im;
-    s[base | lofs[r]] = o;
+    st_amp<R>(&s[base | lofs[r]], cx<R>(re, im));
   }
 }
 
@@ -74,7 +80,11 @@ qs_status launch_fused_dense(qs_sim* s, const int* qubits, int k, const double* 
   QS_CUDA(cudaMemcpyAsync(s->scratch, U, sizeof(double) * 2 * d * d, cudaMemcpyHostToDevice, s->stream));
   const uint64_t ng = 1ull << (s->N - k);
   const unsigned blocks = (unsigned)((ng + TPB - 1) / TPB);
-  if (s->enc == QS_C128) {
+  if (s->enc == QS_C128 && s->c128_df != 0) {
+    size_t smem = sizeof(Cx<DF>) * (size_t)(d * d + TPB * d);
+    QS_CUDA(cudaFuncSetAttribute(k_fused<DF, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fused<DF, double2><<<blocks, TPB, smem, s->stream>>>((double2*)s->state, g, (const double*)s->scratch);
+  } else if (s->enc == QS_C128) {
     size_t smem = sizeof(Cx<double>) * (size_t)(d * d + TPB * d);
     QS_CUDA(cudaFuncSetAttribute(k_fused<double, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_fused<double, double2><<<blocks, TPB, smem, s->stream>>>((double2*)s->state, g, (const double*)s->scratch);

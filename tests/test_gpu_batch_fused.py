@@ -109,14 +109,17 @@ def test_batch_errors(q):
             b.set_circuits([[("CNOT", (1, 1), ())], []])
 
 
-@pytest.mark.parametrize("enc", ["c128", "c64"])
-@pytest.mark.parametrize("k", [1, 2, 3, 5])
-def test_apply_fused_dense(q, enc, k):
-    N = 11
+# complex128 in double-float (mode 1, the default) and on the FP64 units (0)
+@pytest.mark.parametrize("enc,df", [("c128", 1), ("c128", 0), ("c64", 1)])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("N", [11, 16])
+def test_apply_fused_dense(q, enc, df, k, N):
     g = np.random.default_rng(k)
     v0 = g.standard_normal(1 << N) + 1j * g.standard_normal(1 << N)
     v0 /= np.linalg.norm(v0)
     with q.Sim(N, enc) as s:
+        if enc == "c128":
+            s.set_fp64_emulation(df)
         s.copy_in(v0)
         ref = v0.astype(np.complex64).astype(np.complex128) if enc == "c64" else v0.copy()
         for trial in range(3):

@@ -163,11 +163,13 @@ def test_block_product_circuit_n30(q, blocks30, enc, mode):
     free(s)
 
 
+@pytest.mark.parametrize("enc", ["c64", "c128"])
 @pytest.mark.parametrize("qubits", [[3, 9, 17, 22, 29], [29, 0, 15], [28, 2, 20, 1]])
-def test_fused_gate_on_spread_qubits_n30(q, blocks30, qubits):
+def test_fused_gate_on_spread_qubits_n30(q, blocks30, qubits, enc):
     # the dense fused gate on qubits of several blocks, at N = 30 in the
-    # benchmark's launch (tcgen05, gathered groups): the blocks it touches
-    # merge into one (their tensor product, then the gate by the oracle)
+    # benchmark's launch (complex64: tcgen05, gathered groups; complex128:
+    # CUDA cores in double-float): the blocks it touches merge into one
+    # (their tensor product, then the gate by the oracle)
     blocks, recs, states = blocks30
     hit = [i for i, b in enumerate(blocks) if any(x in b for x in qubits)]
     merged = [x for i in hit for x in blocks[i]]
@@ -180,12 +182,12 @@ def test_fused_gate_on_spread_qubits_n30(q, blocks30, qubits):
     sv.apply_dense(mstate, len(merged), [merged.index(x) for x in qubits], U)
     nblocks = [merged] + [b for i, b in enumerate(blocks) if i not in hit]
     nstates = [mstate] + [v for i, v in enumerate(states) if i not in hit]
-    s = q.Sim(N30, "c64")
+    s = q.Sim(N30, enc)
     s.circuit_run(q.gate_array(recs), mode=1)
     s.apply_fused(qubits, U)
     idx = sample_indices(N30, 5)
     got = s.copy_out()[idx]
-    check_amps(got, block_amplitudes(nblocks, nstates, idx), "c64")
+    check_amps(got, block_amplitudes(nblocks, nstates, idx), enc)
     free(s)
 
 
