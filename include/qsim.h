@@ -147,11 +147,12 @@ qs_status sim_set_product_start(qs_sim* sim, int on);
  * the FP32 pipes, which this GPU runs at about 52 times its FP64 rate, in the
  * per-gate sweeps and the tile passes; 0 computes on the FP64 units
  * everywhere; 2 takes double-float in the per-gate sweeps and the FP64 units
- * in the tile passes.  Gates that only move amplitudes or multiply them by +-1, +-i run
- * in FP64 in every mode (exact).  Amplitudes stay FP64 in memory, and every
- * mode agrees with the FP64 oracle to 1e-12.  Reductions and the dense fused
- * gate stay FP64.  Other values give QS_EINVAL.  The paper's
- * double-precision simulator (Sec. 4.1) computes in FP64. */
+ * in the tile passes.  The dense fused gate (apply_fused) computes in
+ * double-float in modes 1 and 2 and on the FP64 units in mode 0.  Gates that
+ * only move amplitudes or multiply them by +-1, +-i run in FP64 in every mode
+ * (exact).  Amplitudes stay FP64 in memory, and every mode agrees with the
+ * FP64 oracle to 1e-12.  Reductions stay FP64.  Other values give QS_EINVAL.
+ * The paper's double-precision simulator (Sec. 4.1) computes in FP64. */
 qs_status sim_set_fp64_emulation(qs_sim* sim, int on);
 
 /* ---- gates (Sec. 2, Eq. (NUM2); Appendix A) ------------------------------ */
@@ -182,17 +183,18 @@ qs_status apply_fused(qs_sim* sim, const int* qubits, int k, const double* U);
  * same product; the tensor-core paths round each operand as x = hi + lo in
  * TF32 and keep the three largest partial products, error near FP32
  * rounding).  The paper has no counterpart: it applies gates one at a time.
- *  QS_FUSED_AUTO       : tcgen05 tensor cores (TMEM accumulators, bulk-copy
- *                        streaming) when 3 <= k <= 5, the qubits are
- *                        0..k-1 in any order and N >= 12; else the mma.sync
- *                        tensor-core kernel when 2 <= k, the qubits are
- *                        0..k-1 and N >= k+4; other qubit sets with
- *                        2 <= k and N >= 12 are first moved to bits 0..k-1
- *                        by permute_qubits (one sweep), the gate runs there
- *                        on tensor cores, and the qubits are moved back (one
- *                        sweep); everything else runs the CUDA-core kernel.
+ *  QS_FUSED_AUTO       : tcgen05 tensor cores (TMEM accumulators) when
+ *                        3 <= k <= 5 and N >= 12, on any k distinct qubits:
+ *                        the qubits 0..k-1 (any order) stream whole groups
+ *                        with TMA tensor copies, other sets gather each
+ *                        group's runs with bulk copies and store from the
+ *                        accumulators; else the mma.sync tensor-core kernel
+ *                        when 2 <= k, the qubits are 0..k-1 and N >= k+4;
+ *                        everything else runs the CUDA-core kernel.
  *  QS_FUSED_CUDA_CORES : the CUDA-core kernel for every gate.
  *  QS_FUSED_MMA_SYNC   : as AUTO without the tcgen05 kernel.
+ * QS_C128 states always take the CUDA-core kernel (see
+ * sim_set_fp64_emulation for its arithmetic).
  * The default is QS_FUSED_AUTO.  Unknown values give QS_EINVAL.  A wait
  * inside the tcgen05 kernel that runs out (about a second) makes
  * apply_fused return QS_ETIMEOUT with the state undefined. */

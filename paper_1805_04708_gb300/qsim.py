@@ -444,8 +444,8 @@ class Sim:
         _check(_lib.sim_set_fused_engine(self._h, self.FUSED_ENGINES[engine]))
 
     def set_product_start(self, on=True):
-        """Product start of complex64 tile runs from a pending |0..0> (see
-        sim_set_product_start); on by default."""
+        """Product start of tile runs from a pending |0..0> (complex64 and
+        complex128; see sim_set_product_start); on by default."""
         _check(_lib.sim_set_product_start(self._h, 1 if on else 0))
 
     def set_fp64_emulation(self, on=1):
