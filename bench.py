@@ -48,8 +48,9 @@ UNIT = "updates/s"
 # N = 26 random-gate circuit in circuit_run mode 2 (after its kernel choice;
 # interpreter and compiled passes), as the mean over a step's 8 passes of
 # which the first only writes, scaled by the 16x units; None when a pass
-# kernel changes after the capture
-TILE_TRAFFIC_PER_PASS = 1.5227e10
+# kernel changes after the capture (the pass kernels' parameter block gained
+# the complex128 product-start fields after the last one, 1.5227e10 B)
+TILE_TRAFFIC_PER_PASS = None
 
 
 def workload_records(N=N_QUBITS, ngates=N_GATES, seed=SEED):
