@@ -164,12 +164,13 @@ def test_block_product_circuit_n30(q, blocks30, enc, mode):
 
 
 @pytest.mark.parametrize("enc", ["c64", "c128"])
-@pytest.mark.parametrize("qubits", [[3, 9, 17, 22, 29], [29, 0, 15], [28, 2, 20, 1]])
+@pytest.mark.parametrize("qubits", [[3, 9, 17, 22, 29], [29, 0, 15], [28, 2, 20, 1], [0, 1, 2, 3, 4], [2, 0, 1]])
 def test_fused_gate_on_spread_qubits_n30(q, blocks30, qubits, enc):
     # the dense fused gate on qubits of several blocks, at N = 30 in the
-    # benchmark's launch (complex64: tcgen05, gathered groups; complex128:
-    # CUDA cores in double-float): the blocks it touches merge into one
-    # (their tensor product, then the gate by the oracle)
+    # benchmark's launches (complex64: tcgen05, gathered groups or, on the
+    # lowest qubits, TMA tensor copies; complex128: CUDA cores in
+    # double-float): the blocks it touches merge into one (their tensor
+    # product, then the gate by the oracle)
     blocks, recs, states = blocks30
     hit = [i for i, b in enumerate(blocks) if any(x in b for x in qubits)]
     merged = [x for i in hit for x in blocks[i]]
